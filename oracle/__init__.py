@@ -1,0 +1,261 @@
+"""FP64 CPU oracle for the altGDmin hot path (Alg. 2 of the paper).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this package.  It wraps the plain C
+library built from `altgdmin_oracle.c` (numpy arrays in, numpy arrays out) and
+shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "altgdmin_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libaltgdmin_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KIND_MRI = 0
+KIND_DENSE = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, OpenMP, no fast-math)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "altgdmin_oracle.h"))):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd, cwd=_HERE)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Problem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("ny", C.c_int32), ("nx", C.c_int32), ("q", C.c_int32),
+                ("nc", C.c_int32), ("smaps", C.c_void_p), ("idx", C.c_void_p), ("fp", C.c_void_p),
+                ("dense", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("trunc_factor", C.c_double), ("energy_pct", C.c_double), ("eta_c", C.c_double),
+                ("eps_exit", C.c_double), ("init_kind", C.c_int32), ("exit_enabled", C.c_int32),
+                ("frob_eta", C.c_int32), ("grad_mode", C.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB_PATH)
+            P = C.POINTER(_Problem)
+            vp, i32, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+            lib.orc_dft2.argtypes = [vp, vp, i32, i32, i32]
+            lib.orc_forward.argtypes = [P, i32, vp, vp]
+            lib.orc_adjoint.argtypes = [P, i32, vp, vp]
+            lib.orc_eigh.argtypes = [vp, i32, vp, vp]
+            lib.orc_eigh.restype = i32
+            lib.orc_qr.argtypes = [vp, i32, i32, vp, vp]
+            lib.orc_qr.restype = i32
+            lib.orc_lstsq.argtypes = [vp, i32, i32, vp, vp]
+            lib.orc_lstsq.restype = i32
+            lib.orc_init.argtypes = [P, vp, C.POINTER(_Params), i32, i32, vp, vp, vp, dp]
+            lib.orc_init.restype = i32
+            lib.orc_bstep.argtypes = [P, vp, vp, i32, vp]
+            lib.orc_bstep.restype = i32
+            lib.orc_grad.argtypes = [P, vp, vp, vp, i32, i32, vp]
+            lib.orc_cost.argtypes = [P, vp, vp, vp, i32]
+            lib.orc_cost.restype = C.c_double
+            lib.orc_iterate.argtypes = [P, vp, C.POINTER(_Params), vp, i32, i32, dp, vp, vp, vp, vp, vp]
+            lib.orc_iterate.restype = i32
+            lib.orc_sd.argtypes = [vp, vp, i32, i32]
+            lib.orc_sd.restype = C.c_double
+            _lib = lib
+    return _lib
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Params:
+    """Alg. 2 constants (blue parameter settings) plus oracle switches."""
+
+    def __init__(self, trunc_factor=36.0, energy_pct=85.0, eta_c=0.14, eps_exit=0.01,
+                 init_kind=0, exit_enabled=False, frob_eta=False, grad_mode=0):
+        self.s = _Params(trunc_factor, energy_pct, eta_c, eps_exit, init_kind, int(exit_enabled),
+                         int(frob_eta), grad_mode)
+
+
+class Operator:
+    """One LRcCS problem: MRI operator A_k = [H_k F D_j]_j, or dense A_k.
+
+    MRI:   Operator.mri(ny, nx, smaps (nc, n), idx int32, frame_ptr int64)
+    dense: Operator.dense(n, [A_1, ..., A_q])  with A_k of shape (m_k, n)
+    """
+
+    def __init__(self, kind, ny, nx, q, nc, smaps, idx, fp, dense):
+        self.kind, self.ny, self.nx, self.q, self.nc = kind, ny, nx, q, nc
+        self.n = ny * nx
+        self._smaps = smaps
+        self._idx = idx
+        self._fp = fp
+        self._dense = dense
+        self.m = np.diff(fp)
+        self.s = _Problem(kind, ny, nx, q, nc, _ptr(smaps), _ptr(idx), _ptr(fp), _ptr(dense))
+
+    @classmethod
+    def mri(cls, ny, nx, smaps, idx, frame_ptr):
+        smaps = _c128(smaps).reshape(-1, ny * nx)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        fp = np.ascontiguousarray(frame_ptr, dtype=np.int64)
+        return cls(KIND_MRI, ny, nx, len(fp) - 1, smaps.shape[0], smaps, idx, fp, None)
+
+    @classmethod
+    def dense(cls, n, mats):
+        fp = np.zeros(len(mats) + 1, dtype=np.int64)
+        fp[1:] = np.cumsum([a.shape[0] for a in mats])
+        d = _c128(np.concatenate([np.asarray(a).reshape(-1, n) for a in mats], axis=0))
+        return cls(KIND_DENSE, 1, n, len(mats), 1, None, None, fp, d)
+
+    @classmethod
+    def from_problem(cls, p):
+        return cls.mri(p.ny, p.nx, p.smaps, p.idx, p.frame_ptr)
+
+    # -- operator -----------------------------------------------------------
+    def rows(self, k: int) -> int:
+        return int(self.nc * self.m[k])
+
+    def yoff(self, k: int) -> int:
+        return int(self.nc * self._fp[k])
+
+    def forward(self, k: int, x) -> np.ndarray:
+        x = _c128(x)
+        out = np.zeros(self.rows(k), dtype=np.complex128)
+        _load().orc_forward(C.byref(self.s), k, _ptr(x), _ptr(out))
+        return out
+
+    def adjoint(self, k: int, yk) -> np.ndarray:
+        yk = _c128(yk)
+        out = np.zeros(self.n, dtype=np.complex128)
+        _load().orc_adjoint(C.byref(self.s), k, _ptr(yk), _ptr(out))
+        return out
+
+    # -- Alg. 2 pieces ------------------------------------------------------
+    def init(self, y, params: Params = None, rank=0, rmax=None, want_x0=False):
+        """Returns dict(U0, sigma, rank, gamma[, X0])."""
+        params = params or Params()
+        y = _c128(y)
+        rmax = rmax or self.q
+        U0 = np.zeros((self.n, rmax), dtype=np.complex128)
+        sig = np.zeros(self.q, dtype=np.float64)
+        X0 = np.zeros((self.n, self.q), dtype=np.complex128) if want_x0 else None
+        g = C.c_double(0.0)
+        r = _load().orc_init(C.byref(self.s), _ptr(y), C.byref(params.s), int(rank), int(rmax),
+                             _ptr(U0), _ptr(sig), _ptr(X0), C.byref(g))
+        if r < 0:
+            raise RuntimeError("oracle init failed")
+        out = dict(U0=np.ascontiguousarray(U0.reshape(-1)[: self.n * r].reshape(self.n, r)),
+                   sigma=sig, rank=r, gamma=g.value)
+        if want_x0:
+            out["X0"] = X0
+        return out
+
+    def bstep(self, y, U) -> np.ndarray:
+        U = _c128(U)
+        r = U.shape[1]
+        y = _c128(y)
+        B = np.zeros((self.q, r), dtype=np.complex128)  # row k = b_k
+        rc = _load().orc_bstep(C.byref(self.s), _ptr(y), _ptr(U), r, _ptr(B))
+        if rc != 0:
+            raise RuntimeError("rank-deficient least squares")
+        return B.T.copy()
+
+    def grad(self, y, U, B, mode=0) -> np.ndarray:
+        U = _c128(U)
+        r = U.shape[1]
+        Bc = _c128(np.asarray(B).T)
+        y = _c128(y)
+        G = np.zeros_like(U)
+        _load().orc_grad(C.byref(self.s), _ptr(y), _ptr(U), _ptr(Bc), r, mode, _ptr(G))
+        return G
+
+    def cost(self, y, U, B) -> float:
+        U = _c128(U)
+        Bc = _c128(np.asarray(B).T)
+        y = _c128(y)
+        return _load().orc_cost(C.byref(self.s), _ptr(y), _ptr(U), _ptr(Bc), U.shape[1])
+
+    def iterate(self, y, U, n_iter, params: Params = None, eta=0.0, history=False):
+        """Run Alg. 2 iterations from U.  Returns dict(U, Uprev, B (r x q), eta,
+        sd, gnorm, iters[, X (iters, n, q)]) with X_t = U_{t-1} B_t."""
+        params = params or Params()
+        U = _c128(U).copy()
+        r = U.shape[1]
+        Bc = np.zeros((self.q, r), dtype=np.complex128)
+        Uprev = np.zeros_like(U)
+        Xh = np.zeros((n_iter, self.n, self.q), dtype=np.complex128) if history else None
+        sd = np.zeros(n_iter)
+        gn = np.zeros(n_iter)
+        e = C.c_double(eta)
+        y = _c128(y)
+        t = _load().orc_iterate(C.byref(self.s), _ptr(y), C.byref(params.s), _ptr(U), r,
+                                int(n_iter), C.byref(e), _ptr(Bc), _ptr(Uprev), _ptr(Xh),
+                                _ptr(sd), _ptr(gn))
+        if t < 0:
+            raise RuntimeError("oracle iterate failed (%d)" % t)
+        out = dict(U=U, Uprev=Uprev, B=Bc.T.copy(), eta=e.value, sd=sd[:t], gnorm=gn[:t], iters=t)
+        if history:
+            out["X"] = Xh[:t]
+        return out
+
+
+def dft2(x, sign=-1) -> np.ndarray:
+    x = _c128(x)
+    ny, nx = x.shape
+    out = np.zeros_like(x)
+    _load().orc_dft2(_ptr(x), _ptr(out), ny, nx, sign)
+    return out
+
+
+def eigh(A):
+    A = _c128(A)
+    q = A.shape[0]
+    w = np.zeros(q)
+    V = np.zeros_like(A)
+    _load().orc_eigh(_ptr(A), q, _ptr(w), _ptr(V))
+    return w, V
+
+
+def qr(A):
+    A = _c128(A)
+    m, r = A.shape
+    Q = np.zeros_like(A)
+    R = np.zeros((r, r), dtype=np.complex128)
+    if _load().orc_qr(_ptr(A), m, r, _ptr(Q), _ptr(R)) != 0:
+        raise RuntimeError("rank deficient")
+    return Q, R
+
+
+def lstsq(M, y):
+    M = _c128(M)
+    m, r = M.shape
+    b = np.zeros(r, dtype=np.complex128)
+    y = _c128(y)
+    if _load().orc_lstsq(_ptr(M), m, r, _ptr(y), _ptr(b)) != 0:
+        raise RuntimeError("rank deficient")
+    return b
+
+
+def sd(U1, U2) -> float:
+    U1, U2 = _c128(U1), _c128(U2)
+    return _load().orc_sd(_ptr(U1), _ptr(U2), U1.shape[0], U1.shape[1])
