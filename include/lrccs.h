@@ -1,0 +1,164 @@
+/*
+ * lrccs.h -- C ABI of liblrccs, a GB300 (sm_103a) implementation of the
+ * altGDmin hot path for low-rank column-wise compressive sensing (LRcCS) in
+ * dynamic MRI (Babu, Lingala, Vaswani, arXiv 2212.09664).
+ *
+ * Problem (Sec. II-A, measurement model): recover the n x q matrix X = U B
+ * (rank r) from y_k = A_k x_k, k = 1..q, with the multi-coil operator
+ *     A_k = [H_k F D_1; ...; H_k F D_C],
+ * F the unitary 2D DFT (forward kernel exp(-2 pi i k x / N), DC at index 0),
+ * D_j = diag(d_j) the coil sensitivities and H_k the sampling of frame k.
+ * The solver is auto-altGDmin (Alg. 2): truncated spectral initialisation,
+ * then per iteration a least-squares B-step, one gradient step on U with
+ * eta = 0.14 / ||grad f(U_0, B_0)||_2, and QR re-orthonormalisation.
+ *
+ * Conventions used by every entry point
+ *   complex     : interleaved float32 pairs (re, im), "complex64", 8 bytes
+ *   pixel index : i = y * nx + x, k-space index i = ky * nx + kx
+ *   U           : n x r, row-major  (element (i, l) at U[i * r + l])
+ *   B           : r x q, column-major, b_k contiguous (element (l, k) at B[k * r + l])
+ *   X           : n x q, column-major, frame k contiguous (element (i, k) at X[k * n + i])
+ *   y           : ragged, frame k / coil j / sample s at y[C * fp[k] + j * m_k + s],
+ *                 m_k = fp[k+1] - fp[k] samples per coil, samples of a frame in
+ *                 ascending k-space index
+ *   pointers    : every d_* pointer is device memory owned by the caller; the
+ *                 library only reads inputs during the call's stream work and
+ *                 writes outputs in place.  The context owns all other memory.
+ *   streams     : all work is ordered on the stream given to lrccs_create.
+ *   errors      : every call returns an lrccs_status; nothing throws or aborts
+ *                 across the ABI.  lrccs_last_error() describes the last failure.
+ *                 Device-side failures (a non-SPD normal matrix, a wait that timed
+ *                 out) are recorded in a device status word and returned by the
+ *                 next call that synchronises (lrccs_init, lrccs_synchronize,
+ *                 lrccs_iterate when info is requested).
+ *
+ * Scope of this build: images with ny, nx multiples of 32 in [32, 256];
+ * rank r <= 16; q <= 256 frames; C <= 64 coils; every frame's mask must be a
+ * union of full phase-encode lines (1D Cartesian sampling, Sec. V); other
+ * masks return LRCCS_E_UNSUPPORTED.
+ */
+#ifndef LRCCS_H
+#define LRCCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrccs_ctx lrccs_ctx;
+
+typedef enum lrccs_status {
+    LRCCS_OK = 0,
+    LRCCS_E_INVALID = 1,          /* bad argument, descriptor or layout */
+    LRCCS_E_NOMEM = 2,            /* device allocation failed */
+    LRCCS_E_CUDA = 3,             /* a CUDA runtime call failed */
+    LRCCS_E_RANK_DEFICIENT = 4,   /* some frame's (A_k U)^H (A_k U) is not SPD, or m_k C < r */
+    LRCCS_E_TIMEOUT = 5,          /* a bounded device wait gave up */
+    LRCCS_E_ADMISSION = 6,        /* not enough free device memory to admit the work */
+    LRCCS_E_STATE = 7,            /* call out of order (e.g. iterate before init) */
+    LRCCS_E_UNSUPPORTED = 8       /* valid input outside this build's scope (see above) */
+} lrccs_status;
+
+typedef struct lrccs_dims {
+    int32_t ny, nx;     /* image size */
+    int32_t q;          /* number of frames */
+    int32_t ncoil;      /* number of coils C */
+    int32_t rank;       /* r > 0 fixes the rank; 0 selects it by the energy rule of Alg. 2 */
+    int32_t rank_max;   /* buffer capacity for the rank (>= rank, <= 16); 0 -> 16 */
+} lrccs_dims;
+
+typedef struct lrccs_params {
+    double trunc_factor;   /* 36   : gamma = 36 * mean |y|^2 over measured entries (Alg. 2, init) */
+    double energy_pct;     /* 85   : b in the rank rule (Alg. 2) */
+    double eta_c;          /* 0.14 : eta = eta_c / ||grad f(U_0, B_0)||_2 (Alg. 2) */
+    double eps_exit;       /* 0.01 : exit when SD(U_{t-1}, U_t)/sqrt(r) < eps_exit (Alg. 2) */
+    int32_t t_max;         /* 70   : iteration cap used by callers that solve to completion */
+    int32_t exit_enabled;  /* 1: lrccs_iterate stops at the exit test (one host sync per iteration) */
+} lrccs_params;
+
+typedef struct lrccs_iter_info {
+    int32_t t;          /* iterations completed since lrccs_init */
+    int32_t exited;     /* 1 if the exit test fired */
+    double eta;         /* step size in use */
+    double sd;          /* SD(U_{t-1}, U_t) of the last iteration */
+    double gnorm;       /* ||grad||_2 of the first iteration (defines eta) */
+} lrccs_iter_info;
+
+/* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off). */
+void lrccs_default_params(lrccs_params *p);
+
+/* Create a context for one problem size on the current CUDA device.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  Allocates every
+ * device buffer the solve needs.  Errors: LRCCS_E_INVALID (dims outside scope),
+ * LRCCS_E_NOMEM, LRCCS_E_CUDA. */
+lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params,
+                          void *cuda_stream, lrccs_ctx **out);
+
+/* Spectral initialisation (Alg. 2, initialisation) from the measurements.
+ *   d_y        : complex64, ragged (see conventions), C * fp[q] entries
+ *   d_frame_ptr: int64, q + 1 offsets fp (samples per coil); must equal the
+ *                running sum of the per-frame sample counts of d_mask
+ *   d_mask     : uint8, q x (ny * nx) bitmap, 1 = sampled, DC at index 0
+ *   d_smaps    : complex64, C x n coil sensitivities d_j
+ *   out_rank   : receives r (fixed, or chosen by the energy rule); may be NULL
+ * Compacts the masks, computes gamma, Z = [A_k^H y_k] and the truncated and
+ * scaled X0, its top-r left singular vectors U_0, and resets t and eta.  The
+ * call blocks until the device work is done.  Inputs are not retained.
+ * Errors: LRCCS_E_INVALID (frame_ptr inconsistent with the mask),
+ * LRCCS_E_UNSUPPORTED (a mask that is not a union of full lines),
+ * LRCCS_E_RANK_DEFICIENT (sigma_r(X0) = 0), LRCCS_E_CUDA. */
+lrccs_status lrccs_init(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
+                        const uint8_t *d_mask, const void *d_smaps, int32_t *out_rank);
+
+/* Run n_iter altGDmin iterations (Alg. 2, GDmin loop): B-step, gradient,
+ * GD step, CholeskyQR2 re-orthonormalisation.  Asynchronous unless info is
+ * non-NULL or exit_enabled is set (then it synchronises and reports the
+ * device status).  After the call, X = U_{t-1} B_t is available through
+ * lrccs_get_factors / lrccs_get_images.  Errors: LRCCS_E_STATE (no init),
+ * LRCCS_E_RANK_DEFICIENT, LRCCS_E_CUDA. */
+lrccs_status lrccs_iterate(lrccs_ctx *ctx, int32_t n_iter, lrccs_iter_info *info);
+
+/* Copy the output pair of the last iteration: d_U <- U_{t-1} (n x r), d_B <- B_t
+ * (r x q), so that X = U B (Alg. 2 output pairing).  Either pointer may be NULL.
+ * Before any iteration, d_U receives U_0 and d_B is left untouched. */
+lrccs_status lrccs_get_factors(lrccs_ctx *ctx, void *d_U, void *d_B);
+
+/* Current subspace estimate U_t (n x r), the input of the next iteration. */
+lrccs_status lrccs_get_subspace(lrccs_ctx *ctx, void *d_U);
+
+/* Materialise X = U_{t-1} B_t into d_X (n x q column-major complex64). */
+lrccs_status lrccs_get_images(lrccs_ctx *ctx, void *d_X);
+
+/* Diagnostics: copy an internal array to caller device memory.
+ *   LRCCS_BUF_Z     Z = [A_k^H y_k]            n x q, row-major (i * q + k)
+ *   LRCCS_BUF_X0    truncated, scaled X0       n x q, row-major
+ *   LRCCS_BUF_GRAD  last gradient              n x r, row-major
+ *   LRCCS_BUF_SIGMA singular values of X0      q float64, descending
+ *   LRCCS_BUF_IDX   compacted sample indices   fp[q] int32 (ascending per frame)
+ *   LRCCS_BUF_SCAL  scalars                    8 float64: gamma, eta, sd, gnorm, mbar, -, -, -
+ * bytes must be at least the array size. */
+typedef enum lrccs_buffer {
+    LRCCS_BUF_Z = 0, LRCCS_BUF_X0 = 1, LRCCS_BUF_GRAD = 2, LRCCS_BUF_SIGMA = 3,
+    LRCCS_BUF_IDX = 4, LRCCS_BUF_SCAL = 5
+} lrccs_buffer;
+lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, size_t bytes);
+
+/* Wait for the context's stream and return any device-side failure. */
+lrccs_status lrccs_synchronize(lrccs_ctx *ctx);
+
+/* Free everything the context owns.  NULL is allowed. */
+void lrccs_destroy(lrccs_ctx *ctx);
+
+/* Text of the last failure on ctx (or of the last lrccs_create failure when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char *lrccs_last_error(const lrccs_ctx *ctx);
+
+const char *lrccs_status_string(lrccs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRCCS_H */

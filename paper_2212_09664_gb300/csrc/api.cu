@@ -1,0 +1,372 @@
+// api.cu -- the C ABI of liblrccs (declared in include/lrccs.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "internal.h"
+#include "lrccs.h"
+
+static std::string g_create_err;
+
+void set_err(lrccs_ctx *c, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+}
+
+cudaError_t configure_kernels_init(int max_smem);
+cudaError_t configure_kernels_iter(int max_smem);
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_err(c, "%s failed: %s", #call, cudaGetErrorString(e_));                 \
+            return LRCCS_E_CUDA;                                                        \
+        }                                                                               \
+    } while (0)
+
+extern "C" void lrccs_default_params(lrccs_params *p) {
+    if (!p) return;
+    p->trunc_factor = 36.0;
+    p->energy_pct = 85.0;
+    p->eta_c = 0.14;
+    p->eps_exit = 0.01;
+    p->t_max = 70;
+    p->exit_enabled = 0;
+}
+
+extern "C" const char *lrccs_status_string(lrccs_status s) {
+    switch (s) {
+        case LRCCS_OK: return "ok";
+        case LRCCS_E_INVALID: return "invalid argument";
+        case LRCCS_E_NOMEM: return "out of device memory";
+        case LRCCS_E_CUDA: return "CUDA error";
+        case LRCCS_E_RANK_DEFICIENT: return "rank deficient";
+        case LRCCS_E_TIMEOUT: return "device wait timed out";
+        case LRCCS_E_ADMISSION: return "admission refused";
+        case LRCCS_E_STATE: return "call out of order";
+        case LRCCS_E_UNSUPPORTED: return "unsupported input";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *lrccs_last_error(const lrccs_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+static void free_all(lrccs_ctx *c) {
+    void *ptrs[] = {c->d_twy, c->d_twx, c->d_smaps, c->d_rowcnt, c->d_rowidx, c->d_framerows, c->d_lineptr,
+                    c->d_rfptr, c->d_rflist, c->d_usedrows, c->d_rowused, c->d_idx, c->d_meta, c->d_status,
+                    c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
+                    c->d_B, c->d_P, c->d_Hpart, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_R1inv, c->d_M};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+static bool dalloc(lrccs_ctx *c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "cudaMalloc(%zu bytes) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+static bool pow_ok(int v) { return v >= 32 && v <= 256 && v % 32 == 0; }
+
+extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params, void *cuda_stream,
+                                     lrccs_ctx **out) {
+    if (!dims || !out) {
+        set_err(nullptr, "lrccs_create: dims and out must be non-null");
+        return LRCCS_E_INVALID;
+    }
+    *out = nullptr;
+    const lrccs_dims d = *dims;
+    int rmax = d.rank_max > 0 ? d.rank_max : (d.rank > 0 ? d.rank : 16);
+    if (!pow_ok(d.ny) || !pow_ok(d.nx) || d.q < 1 || d.q > 128 || d.ncoil < 1 || d.ncoil > 64 || d.rank < 0 ||
+        d.rank > 16 || rmax < 1 || rmax > 16 || (d.rank > 0 && d.rank > rmax) || (d.rank > d.q)) {
+        set_err(nullptr,
+                "lrccs_create: dims outside scope (ny, nx multiples of 32 in [32,256]; q in [1,128]; "
+                "ncoil in [1,64]; 0 <= rank <= rank_max <= 16; rank <= q)");
+        return LRCCS_E_INVALID;
+    }
+    lrccs_ctx *c = new (std::nothrow) lrccs_ctx();
+    if (!c) return LRCCS_E_NOMEM;
+    c->dims = d;
+    if (params) c->prm = *params;
+    else lrccs_default_params(&c->prm);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->ny = d.ny;
+    c->nx = d.nx;
+    c->n = d.ny * d.nx;
+    c->q = d.q;
+    c->nc = d.ncoil;
+    c->rmax = rmax;
+    c->px = d.nx / 32;
+    c->py = d.ny / 32;
+    c->ncg = d.ncoil >= 4 ? 2 : 1;
+    int nblk = (c->n + 127) / 128;
+    if (nblk > 296) nblk = 296;
+    c->nblk = nblk;
+    const int n = c->n, q = c->q, nc = c->nc, ny = c->ny;
+    const int npm = rmax * (rmax + 1) / 2;
+    size_t gcap = (size_t)nblk * rmax * rmax;
+    if ((size_t)c->nx * npm > gcap) gcap = (size_t)c->nx * npm;
+    if ((size_t)152 * q * (q + 1) / 2 > gcap) gcap = (size_t)152 * q * (q + 1) / 2;
+    if (gcap < 1024) gcap = 1024;
+    c->gpart_cap = gcap;
+    c->T_cap = (size_t)nc * n * rmax;
+    bool ok = dalloc(c, &c->d_twy, ny) && dalloc(c, &c->d_twx, c->nx) && dalloc(c, &c->d_smaps, (size_t)nc * n) &&
+              dalloc(c, &c->d_rowcnt, (size_t)q * ny) && dalloc(c, &c->d_rowidx, (size_t)q * ny) &&
+              dalloc(c, &c->d_framerows, (size_t)q * ny) && dalloc(c, &c->d_lineptr, (size_t)q + 1) &&
+              dalloc(c, &c->d_rfptr, (size_t)ny + 1) && dalloc(c, &c->d_rflist, (size_t)q * ny) &&
+              dalloc(c, &c->d_usedrows, (size_t)ny) && dalloc(c, &c->d_rowused, (size_t)ny) &&
+              dalloc(c, &c->d_idx, (size_t)q * n) && dalloc(c, &c->d_meta, (size_t)MT_COUNT + q) &&
+              dalloc(c, &c->d_status, 1) && dalloc(c, &c->d_counters, CNT_COUNT) &&
+              dalloc(c, &c->d_scal, SC_COUNT) && dalloc(c, &c->d_Z, (size_t)n * q) &&
+              dalloc(c, &c->d_X0, (size_t)n * q) && dalloc(c, &c->d_T, c->T_cap) &&
+              dalloc(c, &c->d_U, (size_t)n * rmax) && dalloc(c, &c->d_Uprev, (size_t)n * rmax) &&
+              dalloc(c, &c->d_Up, (size_t)n * rmax) && dalloc(c, &c->d_G, (size_t)n * rmax) &&
+              dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)c->ncg * ny * npm) &&
+              dalloc(c, &c->d_Hpart, (size_t)nblk * q * rmax) && dalloc(c, &c->d_gpart, gcap) &&
+              dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)2 * q * q) &&
+              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_R1inv, (size_t)2 * rmax * rmax) &&
+              dalloc(c, &c->d_M, (size_t)rmax * rmax);
+    if (!ok) {
+        g_create_err = c->err;
+        free_all(c);
+        delete c;
+        return LRCCS_E_NOMEM;
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    c->dev_smem_optin = optin;
+    cudaError_t e = configure_kernels_init(optin);
+    if (e == cudaSuccess) e = configure_kernels_iter(optin);
+    if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
+    if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "lrccs_create: %s", cudaGetErrorString(e));
+        free_all(c);
+        delete c;
+        return LRCCS_E_CUDA;
+    }
+    *out = c;
+    return LRCCS_OK;
+}
+
+extern "C" void lrccs_destroy(lrccs_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+static lrccs_status status_to_code(lrccs_ctx *c, unsigned st) {
+    if (st & ST_PARTIAL_ROWS) {
+        set_err(c, "mask has partially sampled rows; this build supports unions of full phase-encode lines only");
+        return LRCCS_E_UNSUPPORTED;
+    }
+    if (st & ST_FRAMEPTR_MISMATCH) {
+        set_err(c, "frame_ptr does not match the per-frame sample counts of the mask");
+        return LRCCS_E_INVALID;
+    }
+    if (st & ST_ZERO_SIGMA) {
+        set_err(c, "spectral initialisation: sigma_r(X0) = 0 or rank above rank_max");
+        return LRCCS_E_RANK_DEFICIENT;
+    }
+    if (st & ST_NOT_SPD_LS) {
+        set_err(c, "some frame's normal matrix (A_k U)^H (A_k U) is not positive definite");
+        return LRCCS_E_RANK_DEFICIENT;
+    }
+    if (st & ST_NOT_SPD_QR) {
+        set_err(c, "U + eta grad lost rank (CholeskyQR failed)");
+        return LRCCS_E_RANK_DEFICIENT;
+    }
+    if (st & ST_TIMEOUT) {
+        set_err(c, "a bounded device wait timed out");
+        return LRCCS_E_TIMEOUT;
+    }
+    return LRCCS_OK;
+}
+
+static lrccs_status sync_status(lrccs_ctx *c) {
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return status_to_code(c, st);
+}
+
+extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr, const uint8_t *d_mask,
+                                   const void *d_smaps, int32_t *out_rank) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps) {
+        set_err(c, "lrccs_init: null input pointer");
+        return LRCCS_E_INVALID;
+    }
+    c->initialized = 0;
+    c->t = 0;
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->d_meta, 0, MT_COUNT * sizeof(int32_t), c->stream));
+    CK(cudaMemcpyAsync(c->d_smaps, d_smaps, (size_t)c->nc * c->n * sizeof(float2), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    CK(launch_compact(c, d_mask, d_frame_ptr));
+    lrccs_status s = sync_status(c);
+    if (s != LRCCS_OK) return s;
+    int32_t meta[MT_COUNT];
+    CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
+    c->n_used = meta[MT_NUSED];
+    c->n_lines = meta[MT_NLINES];
+    c->total = (int64_t)c->n_lines * c->nx;
+    if (c->total == 0 || c->n_used == 0) {
+        set_err(c, "lrccs_init: no sampled k-space");
+        return LRCCS_E_INVALID;
+    }
+    const size_t need = (size_t)2 * c->nc * c->total;
+    if (need > c->T_cap) {
+        cudaFree(c->d_T);
+        c->d_T = nullptr;
+        if (!dalloc(c, &c->d_T, need)) {
+            c->T_cap = 0;
+            return LRCCS_E_NOMEM;
+        }
+        c->T_cap = need;
+    }
+    CK(launch_energy(c, (const float2 *)d_y));
+    CK(launch_init_adjoint(c, (const float2 *)d_y));
+    CK(launch_gram_x0(c));
+    s = sync_status(c);
+    if (s != LRCCS_OK) return s;
+    CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
+    c->r = meta[MT_RANK];
+    if (c->r < 1 || c->r > c->rmax) {
+        set_err(c, "lrccs_init: rank %d outside [1, rank_max=%d]", c->r, c->rmax);
+        return LRCCS_E_INVALID;
+    }
+    CK(launch_u0(c));
+    CK(launch_qr(c, 0));
+    CK(cudaMemcpyAsync(c->d_Uprev, c->d_U, (size_t)c->n * c->r * sizeof(float2), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    s = sync_status(c);
+    if (s != LRCCS_OK) return s;
+    c->initialized = 1;
+    if (out_rank) *out_rank = c->r;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_info *info) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!c->initialized) {
+        set_err(c, "lrccs_iterate: call lrccs_init first");
+        return LRCCS_E_STATE;
+    }
+    if (n_iter < 0) {
+        set_err(c, "lrccs_iterate: n_iter < 0");
+        return LRCCS_E_INVALID;
+    }
+    int exited = 0;
+    for (int it = 0; it < n_iter; ++it) {
+        CK(launch_iteration(c));
+        c->t += 1;
+        if (c->prm.exit_enabled) {
+            double sd = 0.0;
+            CK(cudaMemcpyAsync(&sd, c->d_scal + SC_SD, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (sd / sqrt((double)c->r) < c->prm.eps_exit) {
+                exited = 1;
+                break;
+            }
+        }
+    }
+    if (info || c->prm.exit_enabled) {
+        lrccs_status s = sync_status(c);
+        double sc[SC_COUNT];
+        CK(cudaMemcpy(sc, c->d_scal, sizeof(sc), cudaMemcpyDeviceToHost));
+        if (info) {
+            info->t = c->t;
+            info->exited = exited;
+            info->eta = sc[SC_ETA];
+            info->sd = sc[SC_SD];
+            info->gnorm = sc[SC_GNORM];
+        }
+        return s;
+    }
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_factors(lrccs_ctx *c, void *d_U, void *d_B) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!c->initialized) {
+        set_err(c, "lrccs_get_factors: call lrccs_init first");
+        return LRCCS_E_STATE;
+    }
+    if (d_U)
+        CK(cudaMemcpyAsync(d_U, c->d_Uprev, (size_t)c->n * c->r * sizeof(float2), cudaMemcpyDeviceToDevice,
+                           c->stream));
+    if (d_B && c->t > 0)
+        CK(cudaMemcpyAsync(d_B, c->d_B, (size_t)c->q * c->r * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_subspace(lrccs_ctx *c, void *d_U) {
+    if (!c || !d_U) return LRCCS_E_INVALID;
+    if (!c->initialized) {
+        set_err(c, "lrccs_get_subspace: call lrccs_init first");
+        return LRCCS_E_STATE;
+    }
+    CK(cudaMemcpyAsync(d_U, c->d_U, (size_t)c->n * c->r * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_images(lrccs_ctx *c, void *d_X) {
+    if (!c || !d_X) return LRCCS_E_INVALID;
+    if (!c->initialized || c->t == 0) {
+        set_err(c, "lrccs_get_images: run at least one iteration first");
+        return LRCCS_E_STATE;
+    }
+    CK(launch_images(c, (float2 *)d_X));
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void *d_dst, size_t bytes) {
+    if (!c || !d_dst) return LRCCS_E_INVALID;
+    const void *src = nullptr;
+    size_t sz = 0;
+    switch (which) {
+        case LRCCS_BUF_Z: src = c->d_Z; sz = (size_t)c->n * c->q * sizeof(float2); break;
+        case LRCCS_BUF_X0: src = c->d_X0; sz = (size_t)c->n * c->q * sizeof(float2); break;
+        case LRCCS_BUF_GRAD: src = c->d_G; sz = (size_t)c->n * (c->r ? c->r : c->rmax) * sizeof(float2); break;
+        case LRCCS_BUF_SIGMA: src = c->d_sigma; sz = (size_t)c->q * sizeof(double); break;
+        case LRCCS_BUF_IDX: src = c->d_idx; sz = (size_t)c->total * sizeof(int32_t); break;
+        case LRCCS_BUF_SCAL: src = c->d_scal; sz = SC_COUNT * sizeof(double); break;
+        default: set_err(c, "lrccs_get_buffer: unknown buffer"); return LRCCS_E_INVALID;
+    }
+    if (bytes < sz) {
+        set_err(c, "lrccs_get_buffer: destination holds %zu bytes, %zu needed", bytes, sz);
+        return LRCCS_E_INVALID;
+    }
+    if (sz) CK(cudaMemcpyAsync(d_dst, src, sz, cudaMemcpyDeviceToDevice, c->stream));
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_synchronize(lrccs_ctx *c) {
+    if (!c) return LRCCS_E_INVALID;
+    return sync_status(c);
+}

@@ -1,0 +1,113 @@
+// internal.h -- context layout and kernel launchers of liblrccs (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lrccs.h"
+
+// Indices into the device scalar array ctx->d_scal (float64).
+enum {
+    SC_GAMMA = 0,   // truncation threshold gamma
+    SC_ETA = 1,     // step size
+    SC_SD = 2,      // SD(U_{t-1}, U_t) of the last iteration
+    SC_GNORM = 3,   // ||grad||_2 of the iteration that set eta
+    SC_MBAR = 4,    // mean samples per coil
+    SC_ETASET = 5,  // 1 once eta is set
+    SC_COUNT = 8
+};
+
+// Indices into the device int array ctx->d_meta.
+enum {
+    MT_NUSED = 0,   // rows sampled by at least one frame
+    MT_NLINES = 1,  // total (frame, line) pairs
+    MT_MMIN = 2,    // min_k m_k
+    MT_MMAX = 3,    // max_k m_k
+    MT_RANK = 4,    // rank chosen by the init
+    MT_COUNT = 8
+};
+
+// Grid-reduction counters.
+enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_GRAD, CNT_QR1, CNT_QR2, CNT_APPLY, CNT_COUNT = 8 };
+
+struct lrccs_ctx {
+    lrccs_dims dims;
+    lrccs_params prm;
+    cudaStream_t stream;
+    int ny, nx, n, q, nc, rmax;
+    int r;             // rank in use (after init)
+    int initialized;   // lrccs_init succeeded
+    int t;             // iterations run since init
+    int px, py;        // nx / 32, ny / 32
+    int ncg;           // coil groups in the forward row pass
+    int nblk;          // blocks of the pixel-parallel kernels
+    int n_used;        // host copy of MT_NUSED
+    int n_lines;       // host copy of MT_NLINES
+    int64_t total;     // fp[q] (samples per coil, all frames)
+    int dev_smem_optin;
+    std::string err;
+
+    // geometry / sampling
+    float2 *d_twy, *d_twx;       // twiddles w_N^t, N = ny / nx
+    float2 *d_smaps;             // nc * n
+    int32_t *d_rowcnt;           // q * ny  samples of frame k in row ky
+    int32_t *d_rowidx;           // q * ny  line index of row ky in frame k, or -1
+    int32_t *d_framerows;        // q * ny  row ky of line i of frame k, at lineptr[k] + i
+    int32_t *d_lineptr;          // q + 1
+    int32_t *d_rfptr;            // ny + 1  frames sampling row ky: rflist[rfptr[ky] .. rfptr[ky+1])
+    int32_t *d_rflist;           // q * ny
+    int32_t *d_usedrows;         // ny      rows sampled by some frame
+    uint8_t *d_rowused;          // ny
+    int32_t *d_idx;              // sample indices (capacity q * n)
+    int32_t *d_meta;             // MT_COUNT ints, then the eigenvalue order (q ints)
+    unsigned int *d_status;      // status word (ST_* bits)
+    unsigned int *d_counters;    // CNT_COUNT
+    double *d_scal;              // SC_COUNT
+
+    // numerical buffers
+    float2 *d_Z;                 // n * q   Z = [A_k^H y_k]   (row-major i*q + k)
+    float2 *d_X0;                // n * q   truncated, scaled X0
+    float2 *d_T;                 // work: nc * n * rmax (iteration), 2 * nc * fp[q] (init)
+    size_t T_cap;                // capacity of d_T in float2
+    float2 *d_U;                 // n * rmax  U_t
+    float2 *d_Uprev;             // n * rmax  U_{t-1}
+    float2 *d_Up;                // n * rmax  gradient, then U+ = U - eta grad
+    float2 *d_G;                 // n * rmax  copy of the last gradient (diagnostics)
+    float2 *d_B;                 // q * rmax
+    float2 *d_P;                 // ncg * ny * npairs row Gram partials
+    float2 *d_Hpart;             // nblk * q * rmax
+    float2 *d_gpart;             // max(nblk, n_col_blocks, gram blocks) * max(npairs, q(q+1)/2)
+    size_t gpart_cap;
+    double *d_sigma;             // q
+    double *d_gram;              // 2 * q * q  X0^H X0 (FP64 re, im)
+    float2 *d_V;                 // q * q eigenvectors of X0^H X0 (columns, sorted)
+    double *d_R1inv;             // r * r
+    float2 *d_M;                 // r * r  (R1 R2)^-1
+};
+
+void set_err(lrccs_ctx *c, const char *fmt, ...);
+
+// ---- launchers (kernels_*.cu). Each enqueues on c->stream and returns the
+// cudaError_t of the launch.
+cudaError_t launch_twiddles(float2 *tw, int N, cudaStream_t s);
+cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d_fp_user);
+cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
+cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
+cudaError_t launch_gram_x0(lrccs_ctx *c);
+cudaError_t launch_u0(lrccs_ctx *c);
+cudaError_t launch_qr(lrccs_ctx *c, int from_grad);   // F, G, H kernels
+cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
+cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);
+int npairs_of(int r);
+
+// Bits of the device status word ctx->d_status.
+enum {
+    ST_FRAMEPTR_MISMATCH = 1 << 0,
+    ST_PARTIAL_ROWS = 1 << 1,
+    ST_NOT_SPD_LS = 1 << 2,
+    ST_NOT_SPD_QR = 1 << 3,
+    ST_ZERO_SIGMA = 1 << 4,
+    ST_TIMEOUT = 1 << 5,
+};

@@ -1,0 +1,470 @@
+// kernels_init.cu -- spectral initialisation of auto-altGDmin (Alg. 2, init)
+// on sm_103a: mask compaction, gamma, Z = [A_k^H y_k], truncated X0, the q x q
+// Gram X0^H X0 with a Jacobi eigensolver, and U_0 = X0 V_r Sigma_r^{-1}.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+// ---------------------------------------------------------------- twiddles
+
+__global__ void k_twiddles(float2 *tw, int N) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) {
+        double s, c;
+        sincospi(-2.0 * (double)t / (double)N, &s, &c);  // exp(-2 pi i t / N)
+        tw[t] = make_float2((float)c, (float)s);
+    }
+}
+
+cudaError_t launch_twiddles(float2 *tw, int N, cudaStream_t s) {
+    k_twiddles<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mask compaction
+// Sampling H_k (Sec. II-A) given as a q x n bitmap.  This build accepts masks
+// whose every row ky is either fully sampled or empty (1D Cartesian lines).
+
+__global__ void k_rowcount(const uint8_t *__restrict__ mask, int rows, int nx, int32_t *rowcnt) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows) return;
+    const uint8_t *m = mask + (size_t)w * nx;
+    int c = 0;
+    for (int x = lane; x < nx; x += 32) c += (m[x] != 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) rowcnt[w] = c;
+}
+
+__global__ void k_structure(const int32_t *__restrict__ rowcnt, const int64_t *__restrict__ fp_user,
+                            int q, int ny, int nx, int32_t *rowidx, int32_t *framerows,
+                            int32_t *lineptr, int32_t *rfptr, int32_t *rflist, int32_t *usedrows,
+                            uint8_t *rowused, int32_t *meta, unsigned int *status, double *scal) {
+    __shared__ int s_lines[129];
+    __shared__ int s_rf[257];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < q; k += blockDim.x) {
+        int L = 0;
+        for (int ky = 0; ky < ny; ++ky) {
+            int c = rowcnt[k * ny + ky];
+            if (c == nx) ++L;
+            else if (c != 0) atomicOr(status, (unsigned)ST_PARTIAL_ROWS);
+        }
+        s_lines[k] = L;
+    }
+    for (int ky = tid; ky < ny; ky += blockDim.x) {
+        int c = 0;
+        for (int k = 0; k < q; ++k) c += (rowcnt[k * ny + ky] == nx);
+        s_rf[ky] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0, mmin = 0x7fffffff, mmax = 0;
+        for (int k = 0; k < q; ++k) {
+            lineptr[k] = acc;
+            int L = s_lines[k];
+            acc += L;
+            mmin = min(mmin, L * nx);
+            mmax = max(mmax, L * nx);
+        }
+        lineptr[q] = acc;
+        meta[MT_NLINES] = acc;
+        meta[MT_MMIN] = mmin;
+        meta[MT_MMAX] = mmax;
+        scal[SC_MBAR] = (double)acc * (double)nx / (double)q;
+        int pacc = 0, nu = 0;
+        for (int ky = 0; ky < ny; ++ky) {
+            rfptr[ky] = pacc;
+            pacc += s_rf[ky];
+            rowused[ky] = (uint8_t)(s_rf[ky] > 0);
+            if (s_rf[ky] > 0) usedrows[nu++] = ky;
+        }
+        rfptr[ny] = pacc;
+        meta[MT_NUSED] = nu;
+        if (fp_user[q] != (int64_t)acc * nx || fp_user[0] != 0) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
+    }
+    __syncthreads();
+    for (int k = tid; k < q; k += blockDim.x) {
+        const int base = lineptr[k];
+        if (fp_user[k] != (int64_t)base * nx) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
+        int i = 0;
+        for (int ky = 0; ky < ny; ++ky) {
+            if (rowcnt[k * ny + ky] == nx) {
+                rowidx[k * ny + ky] = i;
+                framerows[base + i] = ky;
+                ++i;
+            } else {
+                rowidx[k * ny + ky] = -1;
+            }
+        }
+    }
+    for (int ky = tid; ky < ny; ky += blockDim.x) {
+        int base = rfptr[ky], c = 0;
+        for (int k = 0; k < q; ++k)
+            if (rowcnt[k * ny + ky] == nx) rflist[base + c++] = k;
+    }
+}
+
+__global__ void k_fill_idx(const int32_t *__restrict__ framerows, const int32_t *__restrict__ meta,
+                           int nx, int32_t *idx) {
+    const int g = blockIdx.x;
+    if (g >= meta[MT_NLINES]) return;
+    const int ky = framerows[g];
+    for (int kx = threadIdx.x; kx < nx; kx += blockDim.x) idx[(size_t)g * nx + kx] = ky * nx + kx;
+}
+
+cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d_fp_user) {
+    const int rows = c->q * c->ny;
+    k_rowcount<<<(rows * 32 + 255) / 256, 256, 0, c->stream>>>(d_mask, rows, c->nx, c->d_rowcnt);
+    k_structure<<<1, 256, 0, c->stream>>>(c->d_rowcnt, d_fp_user, c->q, c->ny, c->nx, c->d_rowidx,
+                                           c->d_framerows, c->d_lineptr, c->d_rfptr, c->d_rflist,
+                                           c->d_usedrows, c->d_rowused, c->d_meta, c->d_status, c->d_scal);
+    k_fill_idx<<<rows, 128, 0, c->stream>>>(c->d_framerows, c->d_meta, c->nx, c->d_idx);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gamma
+// gamma = trunc * sum |y|^2 / (number of measured entries)  (Alg. 2, init).
+// |y|^2 is formed in FP64 without contraction so that the truncation decision
+// |y|^2 <= gamma is taken on exactly the same squares as an FP64 reference.
+
+LRCCS_DEV double abs2_rn(float2 v) {
+    return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
+}
+
+__global__ void k_energy(const float2 *__restrict__ y, int64_t count, double trunc, double *part,
+                         unsigned int *counter, double *scal) {
+    __shared__ double s_red[32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += abs2_rn(y[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += s_red[w];
+        part[blockIdx.x] = b;
+    }
+    if (last_block_arrive(counter) && threadIdx.x == 0) {
+        double e = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) e += __ldcg(part + b);
+        scal[SC_GAMMA] = trunc * e / (double)count;
+    }
+}
+
+cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y) {
+    const int64_t count = (int64_t)c->nc * c->total;
+    const int blocks = 304;
+    k_energy<<<blocks, 256, 0, c->stream>>>(d_y, count, c->prm.trunc_factor, (double *)c->d_gpart,
+                                            c->d_counters + CNT_ENERGY, c->d_scal);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Z and X0
+// Z[:, k] = A_k^H y_k and X0[:, k] = A_k^H y_k,tnc / sqrt(m_k mbar), computed as
+// a row pass (inverse DFT along kx of every sampled line, both the plain and
+// the truncated data) and a column pass (inverse DFT along ky, coil combine
+// with conj(d_j)).  The line layout of y makes every sampled row contiguous.
+
+template <int P>
+__global__ void __launch_bounds__(256) k_init_rows(const float2 *__restrict__ y, float2 *__restrict__ T0,
+                                                    int64_t total_rows, const double *__restrict__ scal,
+                                                    const float2 *__restrict__ g_tw, float scale) {
+    constexpr int N = 32 * P;
+    __shared__ float2 s_tw[N];
+    load_twiddles(s_tw, g_tw, N);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 4 + (warp >> 1);
+    const int ch = warp & 1;
+    if (g >= total_rows) return;
+    const double gam = scal[SC_GAMMA];
+    const float2 *yr = y + g * N;
+    const int n1 = brev5(lane);
+    float2 v[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+        float2 a = yr[n1 + 32 * m];
+        if (ch == 1 && abs2_rn(a) > gam) a = make_float2(0.f, 0.f);
+        v[m] = a;
+    }
+    warp_fft<P>(v, s_tw, true);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) T0[(g * N + k2 + P * lane) * 2 + ch] = cscale(v[k2], scale);
+}
+
+#define TXI 8
+template <int P>
+__global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0, const float2 *__restrict__ smaps,
+                                                    const int32_t *__restrict__ rowidx,
+                                                    const int32_t *__restrict__ lineptr, const double *__restrict__ scal,
+                                                    float2 *__restrict__ Z, float2 *__restrict__ X0, int nx, int q,
+                                                    int nc, const float2 *__restrict__ g_tw, float scale) {
+    constexpr int NY = 32 * P;
+    constexpr int TP = 2 * TXI + 1;
+    extern __shared__ float2 smem[];
+    float2 *s_tw = smem;
+    float2 *tile = s_tw + NY;
+    float2 *s_S = tile + NY * TP;
+    load_twiddles(s_tw, g_tw, NY);
+    const int k = blockIdx.y, x0 = blockIdx.x * TXI;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n1 = brev5(lane);
+    const int n = NY * nx;
+    const int lp = lineptr[k];
+    const int64_t mk = (int64_t)(lineptr[k + 1] - lp) * nx;
+    const int64_t fbase = (int64_t)nc * lp * nx;
+    float2 acc[2][P];
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc[tt][m] = make_float2(0.f, 0.f);
+    for (int j = 0; j < nc; ++j) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NY * 2 * TXI; e += blockDim.x) {
+            const int yy = e / (2 * TXI), cc = e % (2 * TXI);
+            const int li = rowidx[k * NY + yy];
+            float2 v = make_float2(0.f, 0.f);
+            if (li >= 0) v = T0[(fbase + j * mk + (int64_t)li * nx + x0) * 2 + cc];
+            tile[yy * TP + cc] = v;
+        }
+        for (int e = threadIdx.x; e < NY * TXI; e += blockDim.x)
+            s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXI) * nx + x0 + (e % TXI)];
+        __syncthreads();
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) {
+            const int t = warp + 8 * tt;
+            float2 v[P];
+#pragma unroll
+            for (int m = 0; m < P; ++m) v[m] = tile[(n1 + 32 * m) * TP + t];
+            warp_fft<P>(v, s_tw, true);
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) {
+                const int yy = k2 + P * lane;
+                cfmac(acc[tt][k2], s_S[yy * TXI + (t >> 1)], cscale(v[k2], scale));
+            }
+        }
+    }
+    const double mbar = scal[SC_MBAR];
+    const float xs = (mk > 0) ? (float)(1.0 / sqrt((double)mk * mbar)) : 0.f;
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt) {
+        const int t = warp + 8 * tt;
+        const int xx = t >> 1, ch = t & 1;
+#pragma unroll
+        for (int k2 = 0; k2 < P; ++k2) {
+            const int yy = k2 + P * lane;
+            const size_t i = (size_t)yy * nx + x0 + xx;
+            if (ch == 0) Z[i * q + k] = acc[tt][k2];
+            else X0[i * q + k] = cscale(acc[tt][k2], xs);
+        }
+    }
+}
+
+#define DISPATCH_P(PV, ...)                                           \
+    switch (PV) {                                                      \
+        case 1: { constexpr int P_ = 1; __VA_ARGS__; } break;                 \
+        case 2: { constexpr int P_ = 2; __VA_ARGS__; } break;                 \
+        case 3: { constexpr int P_ = 3; __VA_ARGS__; } break;                 \
+        case 4: { constexpr int P_ = 4; __VA_ARGS__; } break;                 \
+        case 5: { constexpr int P_ = 5; __VA_ARGS__; } break;                 \
+        case 6: { constexpr int P_ = 6; __VA_ARGS__; } break;                 \
+        case 7: { constexpr int P_ = 7; __VA_ARGS__; } break;                 \
+        case 8: { constexpr int P_ = 8; __VA_ARGS__; } break;                 \
+        default: return cudaErrorInvalidValue;                         \
+    }
+
+cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
+    const int64_t total_rows = (int64_t)c->nc * c->n_lines;
+    const float sx = (float)(1.0 / sqrt((double)c->nx));
+    const float sy = (float)(1.0 / sqrt((double)c->ny));
+    const unsigned rb = (unsigned)((total_rows + 3) / 4);
+    if (total_rows > 0) {
+        DISPATCH_P(c->px, (k_init_rows<P_><<<rb, 256, 0, c->stream>>>(d_y, c->d_T, total_rows, c->d_scal,
+                                                                       c->d_twx, sx)));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)c->ny * (1 + 2 * TXI + 1 + TXI) * sizeof(float2);
+    dim3 grid(c->nx / TXI, c->q);
+    DISPATCH_P(c->py, {
+        k_init_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowidx, c->d_lineptr,
+                                                        c->d_scal, c->d_Z, c->d_X0, c->nx, c->q, c->nc,
+                                                        c->d_twy, sy);
+    });
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Gram of X0 and its eigensolver
+
+#define GRAM_CHUNK 32
+#define GRAM_THREADS 512
+#define MAXPP 17   // pairs per thread: q(q+1)/2 <= 512 * 17 for q <= 128
+
+__global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restrict__ X0, int n, int q,
+                                                           float2 *part, unsigned int *counter, double *gram) {
+    extern __shared__ float2 s_x[];  // GRAM_CHUNK * q, then the pair table
+    short2 *s_pair = (short2 *)(s_x + GRAM_CHUNK * q);
+    const int np = q * (q + 1) / 2;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        int a, b;
+        pair_of(p, q, a, b);
+        s_pair[p] = make_short2((short)a, (short)b);
+    }
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    float2 acc[MAXPP];
+#pragma unroll
+    for (int u = 0; u < MAXPP; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int c0 = i0; c0 < i1; c0 += GRAM_CHUNK) {
+        const int cn = min(GRAM_CHUNK, i1 - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cn * q; e += blockDim.x) s_x[e] = X0[(size_t)c0 * q + e];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < MAXPP; ++u) {
+            const int p = threadIdx.x + GRAM_THREADS * u;
+            if (p < np) {
+                const short2 ab = s_pair[p];
+                for (int ii = 0; ii < cn; ++ii) cfmac(acc[u], s_x[ii * q + ab.x], s_x[ii * q + ab.y]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXPP; ++u) {
+        const int p = threadIdx.x + GRAM_THREADS * u;
+        if (p < np) part[(size_t)blockIdx.x * np + p] = acc[u];
+    }
+    if (last_block_arrive(counter)) {
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            double re = 0.0, im = 0.0;
+            for (int b = 0; b < (int)gridDim.x; ++b) {
+                float2 v = __ldcg(part + (size_t)b * np + p);
+                re += v.x;
+                im += v.y;
+            }
+            const short2 ab = s_pair[p];
+            const int a = ab.x, bb = ab.y;
+            gram[2 * (a * q + bb)] = re;
+            gram[2 * (a * q + bb) + 1] = im;
+            gram[2 * (bb * q + a)] = re;
+            gram[2 * (bb * q + a) + 1] = -im;
+        }
+    }
+}
+
+// One block: eigendecomposition of the q x q Gram X0^H X0 (FP64 sums, FP32
+// Jacobi), sigma_j = sqrt(lambda_j) sorted descending, and the rank rule of
+// Alg. 2 when rank_in == 0: the smallest r whose leading sigma^2 reach b% of
+// the energy of the first floor(min(n, q, C min m_k)/10) (at least 1).
+__global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int rank_in, int rmax,
+                      double energy_pct, float2 *V, int32_t *order, double *sigma, int32_t *meta,
+                      unsigned int *status) {
+    extern __shared__ float2 sA[];  // q * q
+    __shared__ float s_c[64], s_s[64];
+    __shared__ float2 s_e[64];
+    __shared__ int s_cnt;
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        sA[e] = make_float2((float)gram[2 * e], (float)gram[2 * e + 1]);
+        V[e] = make_float2((e / q) == (e % q) ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    block_jacobi(sA, q, V, q, s_c, s_s, s_e, &s_cnt, 40);
+    if (threadIdx.x == 0) {
+        // selection sort of the eigenvalue order, descending
+        for (int i = 0; i < q; ++i) order[i] = i;
+        for (int i = 0; i < q; ++i) {
+            int best = i;
+            for (int j = i + 1; j < q; ++j)
+                if (sA[order[j] * q + order[j]].x > sA[order[best] * q + order[best]].x) best = j;
+            int t = order[i];
+            order[i] = order[best];
+            order[best] = t;
+        }
+        for (int i = 0; i < q; ++i) {
+            double lam = (double)sA[order[i] * q + order[i]].x;
+            sigma[i] = sqrt(lam > 0.0 ? lam : 0.0);
+        }
+        int r = rank_in;
+        if (r <= 0) {
+            long long capn = min(n, q);
+            long long cm = (long long)nc * meta[MT_MMIN];
+            if (cm < capn) capn = cm;
+            int cap = (int)(capn / 10);
+            if (cap < 1) cap = 1;
+            double tot = 0.0, acc = 0.0;
+            for (int j = 0; j < cap; ++j) tot += sigma[j] * sigma[j];
+            r = cap;
+            for (int j = 0; j < cap; ++j) {
+                acc += sigma[j] * sigma[j];
+                if (acc >= energy_pct / 100.0 * tot) { r = j + 1; break; }
+            }
+        }
+        meta[MT_RANK] = r;
+        if (r > rmax || r > q) atomicOr(status, (unsigned)ST_ZERO_SIGMA);
+        else if (!(sigma[r - 1] > 0.0)) atomicOr(status, (unsigned)ST_ZERO_SIGMA);
+    }
+}
+
+cudaError_t launch_gram_x0(lrccs_ctx *c) {
+    const int q = c->q;
+    const int np = q * (q + 1) / 2;
+    int blocks = (c->n + 127) / 128;
+    if (blocks > 152) blocks = 152;
+    if ((size_t)blocks * np > c->gpart_cap) blocks = (int)(c->gpart_cap / np);
+    const size_t smem = (size_t)GRAM_CHUNK * q * sizeof(float2) + (size_t)np * sizeof(short2);
+    double *gram = c->d_gram;
+    k_gram_x0<<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart, c->d_counters + CNT_GRAMX0,
+                                                         gram);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem2 = (size_t)q * q * sizeof(float2);
+    k_eig<<<1, 256, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
+                                        c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- U_0
+// U_0 = X0 V_r Sigma_r^{-1}: the top-r left singular vectors of X0 (Alg. 2),
+// written to the U+ buffer and then orthonormalised by CholeskyQR2.
+
+__global__ void k_u0(const float2 *__restrict__ X0, const float2 *__restrict__ V, const int32_t *__restrict__ order,
+                     const double *__restrict__ sigma, int n, int q, int r, float2 *Up) {
+    extern __shared__ float2 s_v[];  // q * r, scaled by 1/sigma
+    for (int e = threadIdx.x; e < q * r; e += blockDim.x) {
+        const int k = e / r, l = e % r;
+        const float is = (float)(1.0 / sigma[l]);
+        s_v[e] = cscale(V[k * q + order[l]], is);
+    }
+    __syncthreads();
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * r; e += gridDim.x * blockDim.x) {
+        const int i = e / r, l = e % r;
+        float2 acc = make_float2(0.f, 0.f);
+        const float2 *xr = X0 + (size_t)i * q;
+        for (int k = 0; k < q; ++k) cfma(acc, xr[k], s_v[k * r + l]);
+        Up[e] = acc;
+    }
+}
+
+cudaError_t launch_u0(lrccs_ctx *c) {
+    const size_t smem = (size_t)c->q * c->r * sizeof(float2);
+    k_u0<<<304, 256, smem, c->stream>>>(c->d_X0, c->d_V, c->d_meta + MT_COUNT, c->d_sigma, c->n, c->q, c->r,
+                                        c->d_Up);
+    return cudaGetLastError();
+}
+
+// Allow every kernel of this file the device's opt-in shared memory per block
+// (the launch still requests only what it needs).
+#define SET_SMEM(fn) do { cudaError_t e_ = allow_smem(fn, max_smem); if (e_ != cudaSuccess) return e_; } while (0)
+cudaError_t configure_kernels_init(int max_smem) {
+    SET_SMEM(k_init_cols<1>); SET_SMEM(k_init_cols<2>); SET_SMEM(k_init_cols<3>); SET_SMEM(k_init_cols<4>);
+    SET_SMEM(k_init_cols<5>); SET_SMEM(k_init_cols<6>); SET_SMEM(k_init_cols<7>); SET_SMEM(k_init_cols<8>);
+    SET_SMEM(k_gram_x0);
+    SET_SMEM(k_eig);
+    SET_SMEM(k_u0);
+    return cudaGetLastError();
+}

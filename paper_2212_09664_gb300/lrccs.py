@@ -1,0 +1,208 @@
+"""Thin ctypes binding of liblrccs (include/lrccs.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors (torch is used for device memory and
+streams); each function has the same name as the C entry point it calls.
+There is no CPU fallback: if the shared library cannot be loaded, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrccs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "liblrccs.so is not built (%s); run `python -c \"import __graft_entry__ as g; g.build()\"`" % LIB_PATH)
+
+_lib = C.CDLL(LIB_PATH)
+
+# status codes (lrccs_status)
+OK, E_INVALID, E_NOMEM, E_CUDA, E_RANK_DEFICIENT, E_TIMEOUT, E_ADMISSION, E_STATE, E_UNSUPPORTED = range(9)
+BUF_Z, BUF_X0, BUF_GRAD, BUF_SIGMA, BUF_IDX, BUF_SCAL = range(6)
+
+
+class Dims(C.Structure):
+    _fields_ = [("ny", C.c_int32), ("nx", C.c_int32), ("q", C.c_int32), ("ncoil", C.c_int32),
+                ("rank", C.c_int32), ("rank_max", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("trunc_factor", C.c_double), ("energy_pct", C.c_double), ("eta_c", C.c_double),
+                ("eps_exit", C.c_double), ("t_max", C.c_int32), ("exit_enabled", C.c_int32)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("t", C.c_int32), ("exited", C.c_int32), ("eta", C.c_double), ("sd", C.c_double),
+                ("gnorm", C.c_double)]
+
+
+_vp = C.c_void_p
+_st = C.c_int
+_sig = {
+    "lrccs_default_params": (None, [C.POINTER(Params)]),
+    "lrccs_create": (_st, [C.POINTER(Dims), C.POINTER(Params), _vp, C.POINTER(_vp)]),
+    "lrccs_init": (_st, [_vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_int32)]),
+    "lrccs_iterate": (_st, [_vp, C.c_int32, C.POINTER(IterInfo)]),
+    "lrccs_get_factors": (_st, [_vp, _vp, _vp]),
+    "lrccs_get_subspace": (_st, [_vp, _vp]),
+    "lrccs_get_images": (_st, [_vp, _vp]),
+    "lrccs_get_buffer": (_st, [_vp, C.c_int, _vp, C.c_size_t]),
+    "lrccs_synchronize": (_st, [_vp]),
+    "lrccs_destroy": (None, [_vp]),
+    "lrccs_last_error": (C.c_char_p, [_vp]),
+    "lrccs_status_string": (C.c_char_p, [_st]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class LrccsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("lrccs status %d (%s): %s" % (
+            status, _lib.lrccs_status_string(status).decode(), msg))
+        self.status = status
+
+
+def _check(ctx, st):
+    if st != OK:
+        raise LrccsError(st, (_lib.lrccs_last_error(ctx) or b"").decode())
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA tensor (no copies are made here)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def default_params() -> Params:
+    p = Params()
+    _lib.lrccs_default_params(C.byref(p))
+    return p
+
+
+def lrccs_create(ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None):
+    """Returns an opaque context handle (int).  `stream` is a torch.cuda.Stream or None."""
+    d = Dims(ny, nx, q, ncoil, rank, rank_max)
+    p = params if params is not None else default_params()
+    h = _vp()
+    s = None if stream is None else _vp(stream.cuda_stream)
+    _check(None, _lib.lrccs_create(C.byref(d), C.byref(p), s, C.byref(h)))
+    return h.value
+
+
+def lrccs_init(ctx, y, frame_ptr, mask, smaps) -> int:
+    r = C.c_int32(0)
+    _check(ctx, _lib.lrccs_init(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps), C.byref(r)))
+    return r.value
+
+
+def lrccs_iterate(ctx, n_iter: int, info: bool = False):
+    inf = IterInfo() if info else None
+    _check(ctx, _lib.lrccs_iterate(ctx, int(n_iter), C.byref(inf) if info else None))
+    if info:
+        return dict(t=inf.t, exited=inf.exited, eta=inf.eta, sd=inf.sd, gnorm=inf.gnorm)
+    return None
+
+
+def lrccs_get_factors(ctx, U=None, B=None):
+    _check(ctx, _lib.lrccs_get_factors(ctx, _ptr(U), _ptr(B)))
+
+
+def lrccs_get_subspace(ctx, U):
+    _check(ctx, _lib.lrccs_get_subspace(ctx, _ptr(U)))
+
+
+def lrccs_get_images(ctx, X):
+    _check(ctx, _lib.lrccs_get_images(ctx, _ptr(X)))
+
+
+def lrccs_get_buffer(ctx, which: int, dst):
+    _check(ctx, _lib.lrccs_get_buffer(ctx, int(which), _ptr(dst), dst.numel() * dst.element_size()))
+
+
+def lrccs_synchronize(ctx):
+    _check(ctx, _lib.lrccs_synchronize(ctx))
+
+
+def lrccs_destroy(ctx):
+    _lib.lrccs_destroy(ctx)
+
+
+def lrccs_last_error(ctx=None) -> str:
+    return (_lib.lrccs_last_error(ctx) or b"").decode()
+
+
+class Solver:
+    """Convenience owner of one context: create -> init -> iterate -> factors.
+
+    All tensors live on the current CUDA device; outputs are new torch tensors.
+    """
+
+    def __init__(self, ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None):
+        import torch
+
+        self._torch = torch
+        self.ny, self.nx, self.q, self.nc = ny, nx, q, ncoil
+        self.n = ny * nx
+        self.stream = stream
+        self.ctx = lrccs_create(ny, nx, q, ncoil, rank, rank_max, params, stream)
+        self.r = rank
+
+    def close(self):
+        if self.ctx:
+            lrccs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, y, frame_ptr, mask, smaps) -> int:
+        self.r = lrccs_init(self.ctx, y, frame_ptr, mask, smaps)
+        return self.r
+
+    def iterate(self, n_iter, info=False):
+        return lrccs_iterate(self.ctx, n_iter, info)
+
+    def factors(self):
+        t = self._torch
+        U = t.empty((self.n, self.r), dtype=t.complex64, device="cuda")
+        B = t.zeros((self.q, self.r), dtype=t.complex64, device="cuda")   # row k = b_k
+        lrccs_get_factors(self.ctx, U, B)
+        return U, B
+
+    def subspace(self):
+        t = self._torch
+        U = t.empty((self.n, self.r), dtype=t.complex64, device="cuda")
+        lrccs_get_subspace(self.ctx, U)
+        return U
+
+    def images(self):
+        t = self._torch
+        X = t.empty((self.q, self.n), dtype=t.complex64, device="cuda")   # row k = x_k
+        lrccs_get_images(self.ctx, X)
+        return X
+
+    def buffer(self, which):
+        t = self._torch
+        shapes = {BUF_Z: ((self.n, self.q), t.complex64), BUF_X0: ((self.n, self.q), t.complex64),
+                  BUF_GRAD: ((self.n, self.r), t.complex64), BUF_SIGMA: ((self.q,), t.float64),
+                  BUF_SCAL: ((8,), t.float64)}
+        shape, dt = shapes[which]
+        out = t.empty(shape, dtype=dt, device="cuda")
+        lrccs_get_buffer(self.ctx, which, out)
+        return out
+
+    def sync(self):
+        lrccs_synchronize(self.ctx)

@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+header declares, and the host-side argument validation works without a GPU."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+LIB = os.path.join(ROOT, "paper_2212_09664_gb300", "liblrccs.so")
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(HEADER_DIR):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(HEADER_DIR, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(lrccs_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    return C.CDLL(LIB)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("lrccs_create", "lrccs_init", "lrccs_iterate", "lrccs_get_factors", "lrccs_destroy",
+                     "lrccs_last_error", "lrccs_synchronize"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = declared_functions() - exported
+    assert not missing, "declared but not exported: %s" % sorted(missing)
+    for name in declared_functions():
+        getattr(lib, name)
+
+
+def test_default_params_are_the_papers(lib):
+    import json
+
+    from paper_2212_09664_gb300 import lrccs
+
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    p = lrccs.default_params()
+    assert p.trunc_factor == g["trunc_factor"]["value"]
+    assert p.energy_pct == g["energy_pct"]["value"]
+    assert p.eta_c == g["eta_c"]["value"]
+    assert p.eps_exit == g["eps_exit"]["value"]
+    assert p.t_max == g["t_max"]["value"]
+
+
+@pytest.mark.parametrize("dims", [
+    (48, 64, 8, 2, 2, 0),     # ny not a multiple of 32
+    (64, 64, 0, 2, 2, 0),     # no frames
+    (64, 64, 8, 2, 17, 0),    # rank above 16
+    (64, 64, 8, 0, 2, 0),     # no coils
+    (64, 64, 4, 1, 5, 0),     # rank above q
+    (512, 64, 8, 1, 2, 0),    # side above 256
+])
+def test_create_rejects_dims_outside_scope(lib, dims):
+    from paper_2212_09664_gb300 import lrccs
+
+    with pytest.raises(lrccs.LrccsError) as ei:
+        lrccs.lrccs_create(*dims)
+    assert ei.value.status == lrccs.E_INVALID
+    assert "scope" in str(ei.value)
+
+
+def test_status_strings(lib):
+    from paper_2212_09664_gb300 import lrccs
+
+    for s in range(9):
+        assert lrccs._lib.lrccs_status_string(s)

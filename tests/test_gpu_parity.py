@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  The CUDA path computes in FP32 (complex64 data, FP32 FFT and
+accumulation, FP64 only for the r x r Cholesky factorisations, gamma and the
+truncation test).  Per-iterate X_t = U_{t-1} B_t must match the oracle within
+relative NRMSE 1e-4; bit-exact results are required for the mask compaction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_09664_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2212_09664_gb300 import lrccs  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL = 1e-4
+
+
+def nrmse(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(p, mask=None, fp=None):
+    return (torch.from_numpy(p.y).to(DEV),
+            torch.from_numpy(p.frame_ptr if fp is None else fp).to(DEV),
+            torch.from_numpy(p.mask if mask is None else mask).to(DEV),
+            torch.from_numpy(p.smaps).to(DEV))
+
+
+def gpu_run(p, n_iter, rank=None, collect=True):
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank if rank is None else rank, rank_max=16 if rank == 0 else 0)
+    r = s.init(*to_dev(p))
+    out = dict(rank=r, U0=s.factors()[0].cpu().numpy(), X=[], infos=[])
+    for _ in range(n_iter):
+        out["infos"].append(s.iterate(1, info=True))
+        if collect:
+            U, B = s.factors()
+            out["X"].append((U @ B.T).cpu().numpy().astype(np.complex128))
+    out["solver"] = s
+    return out
+
+
+def oracle_run(p, n_iter, rank=None):
+    op = oracle.Operator.from_problem(p)
+    ini = op.init(p.y, rank=p.rank if rank is None else rank, want_x0=True)
+    it = op.iterate(p.y, ini["U0"], n_iter, history=True)
+    return op, ini, it
+
+
+MEDIUM = dict(kind="phantom", ny=96, nx=64, q=20, nc=4, rank=3, mask_kind="lines_vd", accel=4.0, noise=0.01)
+
+
+# ---------------------------------------------------------------- compaction (bit-exact)
+
+@pytest.mark.parametrize("spec", ["lines64_q32_c1_r4", "cardiac192_q48_c12_r10"])
+def test_mask_compaction_bit_exact(spec):
+    p = synth.make_problem(spec)
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank)
+    s.init(*to_dev(p))
+    idx = torch.empty(int(p.frame_ptr[-1]), dtype=torch.int32, device=DEV)
+    lrccs.lrccs_get_buffer(s.ctx, lrccs.BUF_IDX, idx)
+    assert np.array_equal(idx.cpu().numpy(), p.idx)
+    s.close()
+
+
+def test_frame_ptr_mismatch_is_rejected():
+    p = synth.make_problem("lines64_q32_c1_r4")
+    fp = p.frame_ptr.copy()
+    fp[3] += 64
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank)
+    with pytest.raises(lrccs.LrccsError) as ei:
+        s.init(*to_dev(p, fp=fp))
+    assert ei.value.status == lrccs.E_INVALID
+    s.close()
+
+
+def test_partial_rows_are_unsupported():
+    p = synth.make_problem("lines64_q32_c1_r4")
+    mask = p.mask.copy()
+    mask[0, 5] ^= 1                        # break one line
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank)
+    with pytest.raises(lrccs.LrccsError) as ei:
+        s.init(*to_dev(p, mask=mask))
+    assert ei.value.status == lrccs.E_UNSUPPORTED
+    s.close()
+
+
+def test_empty_frame_is_rank_deficient():
+    p = synth.make_problem(MEDIUM, seed=3)
+    mask = p.mask.copy()
+    mask[4] = 0                            # frame 4 has no samples at all
+    idx, fp = synth.compact_mask(mask)
+    # keep y consistent with the new layout: drop frame 4's samples
+    keep = np.ones(p.y.size, bool)
+    keep[p.nc * p.frame_ptr[4]: p.nc * p.frame_ptr[5]] = False
+    q = synth.Problem(p.name, p.ny, p.nx, p.q, p.nc, p.rank, p.t_iter, mask, idx, fp, p.y[keep].copy(),
+                      p.smaps, {})
+    s = lrccs.Solver(q.ny, q.nx, q.q, q.nc, q.rank)
+    s.init(*to_dev(q))
+    with pytest.raises(lrccs.LrccsError) as ei:
+        s.iterate(1, info=True)
+    assert ei.value.status == lrccs.E_RANK_DEFICIENT
+    s.close()
+
+
+# ---------------------------------------------------------------- initialisation
+
+@pytest.mark.parametrize("spec", ["lines64_q32_c1_r4", "medium"])
+def test_init_parity(spec):
+    p = synth.make_problem(MEDIUM if spec == "medium" else spec, seed=7 if spec == "medium" else None)
+    op, ini, _ = oracle_run(p, 0)
+    g = gpu_run(p, 0)
+    s = g["solver"]
+    Z = s.buffer(lrccs.BUF_Z).cpu().numpy()
+    Zr = np.stack([op.adjoint(k, p.y_frame(k).reshape(-1)) for k in range(p.q)], 1)
+    assert nrmse(Z, Zr) < 1e-5                                     # Z = [A_k^H y_k]
+    X0 = s.buffer(lrccs.BUF_X0).cpu().numpy()
+    assert nrmse(X0, ini["X0"]) < 1e-5
+    scal = s.buffer(lrccs.BUF_SCAL).cpu().numpy()
+    assert abs(scal[0] - ini["gamma"]) <= 1e-12 * ini["gamma"]     # gamma in FP64
+    sig = s.buffer(lrccs.BUF_SIGMA).cpu().numpy()
+    r = p.rank
+    assert np.abs(sig[:r] - ini["sigma"][:r]).max() < 1e-4 * ini["sigma"][0]
+    U0 = g["U0"].astype(np.complex128)
+    assert np.abs(U0.conj().T @ U0 - np.eye(r)).max() < 1e-5
+    assert oracle.sd(ini["U0"], U0) < 1e-4
+    s.close()
+
+
+def test_auto_rank_matches_oracle():
+    p = synth.make_problem(MEDIUM, seed=11)
+    op = oracle.Operator.from_problem(p)
+    ini = op.init(p.y, rank=0)
+    g = gpu_run(p, 0, rank=0)
+    assert g["rank"] == ini["rank"]
+    g["solver"].close()
+
+
+# ---------------------------------------------------------------- iterations
+
+def _check_iterates(p, n_iter, tol=TOL):
+    _, _, it = oracle_run(p, n_iter)
+    g = gpu_run(p, n_iter)
+    errs = [nrmse(g["X"][t], it["X"][t]) for t in range(n_iter)]
+    assert max(errs) < tol, "per-iterate NRMSE %s" % np.array2string(np.array(errs), precision=2)
+    assert abs(g["infos"][0]["eta"] - it["eta"]) < 1e-5 * it["eta"]
+    sd_gpu = np.array([i["sd"] for i in g["infos"]])
+    assert np.abs(sd_gpu - it["sd"]).max() < 1e-3
+    g["solver"].close()
+    return errs
+
+
+def test_iterates_single_coil_50():
+    """64 x 64, q = 32, C = 1, r = 4, 16 of 64 lines: 50 iterations."""
+    _check_iterates(synth.make_problem("lines64_q32_c1_r4"), 50)
+
+
+def test_iterates_multicoil_rectangular():
+    """96 x 64 (ny != nx), q = 20, C = 4, r = 3, variable-density lines, noisy phantom."""
+    _check_iterates(synth.make_problem(MEDIUM, seed=5), 20)
+
+
+def test_iterates_ragged_line_counts():
+    """Frames with different numbers of lines (ragged m_k), 128 x 32 image, 5 coils."""
+    rng = np.random.default_rng(21)
+    ny, nx, q = 128, 32, 12
+    mask = np.zeros((q, ny, nx), np.uint8)
+    for k in range(q):
+        nl = 10 + (k * 7) % 23
+        lines = np.concatenate([[0, 1, ny - 1], rng.choice(np.arange(2, ny - 1), nl, replace=False)])
+        mask[k, lines] = 1
+    spec = dict(kind="phantom", ny=ny, nx=nx, q=q, nc=5, rank=2, noise=0.01, mask_kind="full")
+    p0 = synth.make_problem(spec, seed=22)
+    smaps, modes, coef = synth.coil_maps(np.random.default_rng(23), ny, nx, 5)
+    p = synth.assemble("ragged", ny, nx, q, 5, 2, 10, mask.reshape(q, -1), p0.truth["spectra"], modes, coef,
+                       smaps, rng, 0.01, {})
+    assert len(set(np.diff(p.frame_ptr))) > 3
+    _check_iterates(p, 10)
+
+
+def test_iterates_min_and_max_sides():
+    """Smallest (32) and largest (256) supported sides in one problem: 256 x 32."""
+    spec = dict(kind="phantom", ny=256, nx=32, q=6, nc=2, rank=2, mask_kind="lines_vd", accel=4.0, noise=0.01)
+    _check_iterates(synth.make_problem(spec, seed=8), 6)
+
+
+def test_gradient_and_invariants():
+    p = synth.make_problem(MEDIUM, seed=9)
+    op, ini, it = oracle_run(p, 1)
+    g = gpu_run(p, 1)
+    s = g["solver"]
+    G = s.buffer(lrccs.BUF_GRAD).cpu().numpy().astype(np.complex128)
+    U0 = g["U0"].astype(np.complex128)
+    B1 = op.bstep(p.y, U0)
+    Gr = op.grad(p.y, U0, B1)
+    assert nrmse(G, Gr) < 1e-4
+    # LS optimality U^H grad = 0 and orthonormality after CholeskyQR2
+    assert np.linalg.norm(U0.conj().T @ G) / np.linalg.norm(G) < 1e-4
+    U1 = s.subspace().cpu().numpy().astype(np.complex128)
+    assert np.abs(U1.conj().T @ U1 - np.eye(p.rank)).max() < 1e-5
+    s.close()
+
+
+def test_full_size_cardiac_first_iterates():
+    """192 x 192, q = 48, C = 12, r = 10 (the benchmark workload): init and the
+    first 3 iterates against the oracle, then 50 iterations stay orthonormal."""
+    p = synth.make_problem("cardiac192_q48_c12_r10")
+    errs = _check_iterates(p, 3)
+    assert max(errs) < TOL
+    g = gpu_run(p, 50, collect=False)
+    U = g["solver"].subspace().cpu().numpy().astype(np.complex128)
+    assert np.abs(U.conj().T @ U - np.eye(p.rank)).max() < 1e-5
+    g["solver"].close()
+
+
+def test_images_match_factors():
+    p = synth.make_problem(MEDIUM, seed=10)
+    g = gpu_run(p, 2)
+    s = g["solver"]
+    X = s.images().cpu().numpy()        # (q, n): row k = x_k
+    assert nrmse(X.T, g["X"][-1]) < 1e-6
+    s.close()
