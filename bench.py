@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the altGDmin hot path (Alg. 2: spectral init + 50 GDmin
+iterations) on the cardiac-shaped synthetic workload 192 x 192, q = 48 frames,
+12 coils, rank 10, 8x variable-density Cartesian lines, 1% noise.
+
+One step = one full solve through the C ABI: lrccs_init (mask compaction,
+gamma, Z and X0, eigendecomposition, U0) + lrccs_iterate(50) + lrccs_get_factors.
+Metric: frame-iterations/s = q * 50 / (step time), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrccs|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this work has)
+on a bounded sample of the same workload and extrapolates to a 50-iteration
+solve.  Under torchrun (N > 1) every rank solves its own replica of the
+workload (the path is run as independent replicas; nothing is exchanged).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cardiac192_q48_c12_r10"
+T_ITER = 50
+METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
+UNIT = "frame-iterations/s"
+FLUSH_BYTES = 256 << 20            # > 129 MB L2
+ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_gd_gram",
+                "k_rinv_gram", "k_apply"]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_bytes(name, p, r, n_used):
+    """Algorithmic (compulsory) bytes of one launch of an iteration kernel,
+    complex64 = 8 B.  n_u = sampled rows x nx (k-space rows kept between passes)."""
+    n, q, C = p.n, p.q, p.nc
+    nu = n_used * p.nx
+    b = {
+        "k_fwd_cols": n * r + C * n + C * r * nu,        # read U, d_j; write F_y(d_j o U) on sampled rows
+        "k_fwd_rows": 2 * C * r * nu,                    # read + write the sampled rows (in place)
+        "k_adj_rows": 2 * C * r * nu,                    # read FU, write F_x^H(FU W)
+        "k_adj_cols": C * r * nu + C * n + n * q + n * r,  # read rows, d_j, Z; write grad
+        "k_gd_gram": 3 * n * r,                          # read U, grad; write U+
+        "k_rinv_gram": n * r,                            # read U+
+        "k_apply": 4 * n * r + n * q,                    # read U+, U, Z; write U, U_{t-1}
+        "k_solve": 0,
+    }.get(name, 0)
+    return 8 * b
+
+
+def iteration_bytes(p, r, n_used):
+    return sum(kernel_bytes(k, p, r, n_used) for k in ITER_KERNELS)
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels_iter.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2212_09664_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None
+    when there is none or the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "%s_cardiac192.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != source_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(rows))
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores (bounded sample per step)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2212_09664_gb300 import synth
+
+    p = synth.make_problem(WORKLOAD)
+    op = oracle.Operator.from_problem(p)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    ms = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ini = op.init(p.y, rank=p.rank)
+        t1 = time.perf_counter()
+        op.iterate(p.y, ini["U0"], 1)
+        t2 = time.perf_counter()
+        if s >= args.warmup:
+            ms.append(1e3 * ((t1 - t0) + T_ITER * (t2 - t1)))
+    ms_step = float(np.mean(ms))
+    value = p.q * T_ITER / (ms_step / 1e3)
+    sample = ("per step: oracle init + 1 GDmin iteration of the %s workload; the %d-iteration solve time "
+              "is extrapolated as t_init + %d t_iter" % (WORKLOAD, T_ITER, T_ITER))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, ny=p.ny, nx=p.nx, q=p.q, coils=p.nc, rank=p.rank,
+                            iterations=T_ITER),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(p, y_ref_X2):
+    """Oracle timing on a bounded sample (init + 2 iterations), plus the
+    NRMSE of the GPU's X_2 against the oracle's X_2 on the same inputs."""
+    import numpy as np
+
+    import oracle
+
+    op = oracle.Operator.from_problem(p)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    ini = op.init(p.y, rank=p.rank)
+    t1 = time.perf_counter()
+    it = op.iterate(p.y, ini["U0"], 2, history=True)
+    t2 = time.perf_counter()
+    t_iter = (t2 - t1) / 2
+    value = p.q * T_ITER / ((t1 - t0) + T_ITER * t_iter)
+    Xr = it["X"][1]
+    nrmse = float(np.linalg.norm(y_ref_X2 - Xr) / np.linalg.norm(Xr))
+    return dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                sample="oracle init + 2 GDmin iterations of %s (%.1f s); the %d-iteration solve is "
+                       "extrapolated as t_init + %d t_iter" % (WORKLOAD, t2 - t0, T_ITER, T_ITER)), nrmse
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lrccs", choices=["lrccs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs, synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = synth.make_problem(WORKLOAD)
+    stream = torch.cuda.Stream(device=dev)
+    y = torch.from_numpy(p.y).to(dev)
+    fp = torch.from_numpy(p.frame_ptr).to(dev)
+    mask = torch.from_numpy(p.mask).to(dev)
+    sm = torch.from_numpy(p.smaps).to(dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    U = torch.empty((p.n, p.rank), dtype=torch.complex64, device=dev)
+    B = torch.empty((p.q, p.rank), dtype=torch.complex64, device=dev)
+
+    def step():
+        lrccs.lrccs_init(s.ctx, y, fp, mask, sm)
+        lrccs.lrccs_iterate(s.ctx, T_ITER)
+        lrccs.lrccs_get_factors(s.ctx, U, B)
+
+    torch.cuda.synchronize()
+    # warm-up, with every kernel timed once to find the dominant one
+    lrccs.lrccs_profile(s.ctx, "*")
+    for _ in range(args.warmup):
+        step()
+    stats = lrccs.lrccs_profile_read(s.ctx)
+    n_used = int(p.mask.reshape(p.q, p.ny, p.nx)[:, :, 0].any(0).sum())
+    it_stats = [d for d in stats if d["name"] in ITER_KERNELS and d["timed"] > 0]
+    dominant = max(it_stats, key=lambda d: d["ms"])["name"]
+    lrccs.lrccs_profile_reset(s.ctx)
+    lrccs.lrccs_profile(s.ctx, dominant)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                     # L2 flush between timed steps (outside the events)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_steps = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    tot_ms = float(sum(t_steps))
+    prof = lrccs.lrccs_profile_read(s.ctx)
+    launches = int(sum(d["launches"] for d in prof))
+    dom = [d for d in prof if d["name"] == dominant][0]
+    dom_ms = dom["ms"] / max(dom["timed"], 1)
+    lrccs.lrccs_profile(s.ctx, None)
+
+    # end to end through the public API: pinned host inputs -> device, solve, factors -> host
+    yh, fph, mh, smh = (t.cpu().pin_memory() for t in (y, fp, mask, sm))
+    Uh = torch.empty(U.shape, dtype=U.dtype).pin_memory()
+    Bh = torch.empty(B.shape, dtype=B.dtype).pin_memory()
+    yd, fpd, md, smd = (torch.empty_like(t) for t in (y, fp, mask, sm))
+    n_e2e = max(3, min(args.steps, 30))
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(n_e2e)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(n_e2e)]
+    barrier()
+    for i in range(n_e2e):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e_s[i].record(stream)
+            for dst, src in ((yd, yh), (fpd, fph), (md, mh), (smd, smh)):
+                dst.copy_(src, non_blocking=True)
+            lrccs.lrccs_init(s.ctx, yd, fpd, md, smd)
+            lrccs.lrccs_iterate(s.ctx, T_ITER)
+            lrccs.lrccs_get_factors(s.ctx, U, B)
+            Uh.copy_(U, non_blocking=True)
+            Bh.copy_(B, non_blocking=True)
+            e_e[i].record(stream)
+        stream.synchronize()
+    barrier()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in zip(e_s, e_e)))
+    h2d = sum(t.numel() * t.element_size() for t in (y, fp, mask, sm))
+    d2h = sum(t.numel() * t.element_size() for t in (U, B))
+
+    # max over ranks
+    if dist is not None:
+        tt = torch.tensor([tot_ms, e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms, e2e_ms = float(tt[0]), float(tt[1])
+    work = ws * p.q * T_ITER
+    value = work * args.steps / (tot_ms / 1e3)
+    e2e_value = work * n_e2e / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    alg = kernel_bytes(dominant, p, p.rank, n_used)
+    achieved = alg / (dom_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dominant)
+    roof = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
+                kernel=dominant, peak_source=peak_kind, alg_bytes_per_launch=alg, avg_launch_us=dom_ms * 1e3)
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=tot_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(workload=WORKLOAD, ny=p.ny, nx=p.nx, q=p.q, coils=p.nc, rank=p.rank,
+                            iterations=T_ITER, sampled_rows=n_used, l2="flushed between timed steps (256 MB write)",
+                            parallelism="replicas" if ws > 1 else "single GPU"),
+                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                gpu_launches=launches, roofline=roof,
+                clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
+                            samples=clk["samples"]),
+                iteration_bytes=iteration_bytes(p, p.rank, n_used),
+                p99_minibatch_latency_ms=None)
+    if ws == 1 and not args.no_cpu_baseline:
+        # X_2 of the GPU for the parity figure reported beside the oracle timing
+        lrccs.lrccs_init(s.ctx, y, fp, mask, sm)
+        lrccs.lrccs_iterate(s.ctx, 2)
+        lrccs.lrccs_get_factors(s.ctx, U, B)
+        X2 = (U @ B.T).cpu().numpy().astype(np.complex128)
+        cb, nr = cpu_baseline(p, X2)
+        line["cpu_baseline"] = cb
+        line["nrmse_x2_vs_fp64"] = nr
+    s.close()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,23 @@ typedef enum lrccs_buffer {
 } lrccs_buffer;
 lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, size_t bytes);
 
+/* Kernel profiling (measurement support; the paper reports per-step timing
+ * markers, Sec. V).  Launch counts of every kernel are kept always.  CUDA-event
+ * timing is recorded, on the context's stream, around every later launch of the
+ * kernels whose name contains `pattern` ("*" = all; NULL or "" = none).
+ * lrccs_profile_read synchronises the stream, folds the pending events into the
+ * totals and fills up to `max` entries of `out` (one per kernel, in a fixed
+ * order); *count receives the number of kernels.  Names are static strings. */
+typedef struct lrccs_kernel_stat {
+    const char *name;     /* kernel name */
+    int64_t launches;     /* launches since the last reset */
+    int64_t timed;        /* launches that were timed */
+    double ms;            /* summed CUDA-event time of the timed launches */
+} lrccs_kernel_stat;
+lrccs_status lrccs_profile(lrccs_ctx *ctx, const char *pattern);
+lrccs_status lrccs_profile_read(lrccs_ctx *ctx, lrccs_kernel_stat *out, int32_t max, int32_t *count);
+lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
+
 /* Wait for the context's stream and return any device-side failure. */
 lrccs_status lrccs_synchronize(lrccs_ctx *ctx);
 

@@ -174,6 +174,11 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
 extern "C" void lrccs_destroy(lrccs_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    for (const prof_rec &r : c->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     free_all(c);
     delete c;
 }
@@ -364,6 +369,91 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
     }
     if (sz) CK(cudaMemcpyAsync(d_dst, src, sz, cudaMemcpyDeviceToDevice, c->stream));
     return LRCCS_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+
+const char *const kKernelNames[KID_COUNT] = {
+    "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
+    "k_eig", "k_u0", "k_gd_gram", "k_rinv_gram", "k_apply", "k_fwd_cols", "k_fwd_rows", "k_solve",
+    "k_adj_rows", "k_adj_cols", "k_images"};
+
+static cudaEvent_t get_event(lrccs_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(lrccs_ctx *c, int kid) {
+    c->launches[kid] += 1;
+    if (c->prof_mask & (1ull << kid)) {
+        prof_rec r;
+        r.kid = kid;
+        r.a = get_event(c);
+        r.b = get_event(c);
+        cudaEventRecord(r.a, c->stream);
+        c->pending.push_back(r);
+    }
+}
+
+void prof_end(lrccs_ctx *c, int kid) {
+    if ((c->prof_mask & (1ull << kid)) && !c->pending.empty()) cudaEventRecord(c->pending.back().b, c->stream);
+}
+
+static lrccs_status prof_fold(lrccs_ctx *c) {
+    CK(cudaStreamSynchronize(c->stream));
+    for (const prof_rec &r : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.kid] += ms;
+            c->timed[r.kid] += 1;
+        }
+        c->event_pool.push_back(r.a);
+        c->event_pool.push_back(r.b);
+    }
+    c->pending.clear();
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_profile(lrccs_ctx *c, const char *pattern) {
+    if (!c) return LRCCS_E_INVALID;
+    unsigned long long m = 0;
+    if (pattern && *pattern) {
+        for (int k = 0; k < KID_COUNT; ++k)
+            if (!strcmp(pattern, "*") || strstr(kKernelNames[k], pattern)) m |= 1ull << k;
+    }
+    c->prof_mask = m;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_profile_read(lrccs_ctx *c, lrccs_kernel_stat *out, int32_t max, int32_t *count) {
+    if (!c) return LRCCS_E_INVALID;
+    lrccs_status s = prof_fold(c);
+    if (s != LRCCS_OK) return s;
+    for (int k = 0; k < KID_COUNT && k < max && out; ++k) {
+        out[k].name = kKernelNames[k];
+        out[k].launches = c->launches[k];
+        out[k].timed = c->timed[k];
+        out[k].ms = c->prof_ms[k];
+    }
+    if (count) *count = KID_COUNT;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_profile_reset(lrccs_ctx *c) {
+    if (!c) return LRCCS_E_INVALID;
+    lrccs_status s = prof_fold(c);
+    for (int k = 0; k < KID_COUNT; ++k) {
+        c->launches[k] = 0;
+        c->timed[k] = 0;
+        c->prof_ms[k] = 0.0;
+    }
+    return s;
 }
 
 extern "C" lrccs_status lrccs_synchronize(lrccs_ctx *c) {

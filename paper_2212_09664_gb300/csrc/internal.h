@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lrccs.h"
 
@@ -32,7 +33,28 @@ enum {
 // Grid-reduction counters.
 enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_GRAD, CNT_QR1, CNT_QR2, CNT_APPLY, CNT_COUNT = 8 };
 
+// Kernel ids (launch counting and optional CUDA-event timing).
+enum {
+    KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
+    KID_EIG, KID_U0, KID_GD_GRAM, KID_RINV_GRAM, KID_APPLY, KID_FWD_COLS, KID_FWD_ROWS, KID_SOLVE,
+    KID_ADJ_ROWS, KID_ADJ_COLS, KID_IMAGES, KID_COUNT
+};
+extern const char *const kKernelNames[KID_COUNT];
+
+struct prof_rec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
 struct lrccs_ctx {
+    // profiling: launches counted always; kernels in prof_mask timed with events
+    long long launches[KID_COUNT];
+    long long timed[KID_COUNT];
+    double prof_ms[KID_COUNT];
+    unsigned long long prof_mask;
+    std::vector<prof_rec> pending;
+    std::vector<cudaEvent_t> event_pool;
+
     lrccs_dims dims;
     lrccs_params prm;
     cudaStream_t stream;
@@ -88,6 +110,8 @@ struct lrccs_ctx {
 };
 
 void set_err(lrccs_ctx *c, const char *fmt, ...);
+void prof_begin(lrccs_ctx *c, int kid);
+void prof_end(lrccs_ctx *c, int kid);
 
 // ---- launchers (kernels_*.cu). Each enqueues on c->stream and returns the
 // cudaError_t of the launch.

@@ -117,11 +117,17 @@ __global__ void k_fill_idx(const int32_t *__restrict__ framerows, const int32_t 
 
 cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d_fp_user) {
     const int rows = c->q * c->ny;
+    prof_begin(c, KID_ROWCOUNT);
     k_rowcount<<<(rows * 32 + 255) / 256, 256, 0, c->stream>>>(d_mask, rows, c->nx, c->d_rowcnt);
+    prof_end(c, KID_ROWCOUNT);
+    prof_begin(c, KID_STRUCTURE);
     k_structure<<<1, 256, 0, c->stream>>>(c->d_rowcnt, d_fp_user, c->q, c->ny, c->nx, c->d_rowidx,
                                            c->d_framerows, c->d_lineptr, c->d_rfptr, c->d_rflist,
                                            c->d_usedrows, c->d_rowused, c->d_meta, c->d_status, c->d_scal);
+    prof_end(c, KID_STRUCTURE);
+    prof_begin(c, KID_FILL_IDX);
     k_fill_idx<<<rows, 128, 0, c->stream>>>(c->d_framerows, c->d_meta, c->nx, c->d_idx);
+    prof_end(c, KID_FILL_IDX);
     return cudaGetLastError();
 }
 
@@ -160,8 +166,10 @@ __global__ void k_energy(const float2 *__restrict__ y, int64_t count, double tru
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y) {
     const int64_t count = (int64_t)c->nc * c->total;
     const int blocks = 304;
+    prof_begin(c, KID_ENERGY);
     k_energy<<<blocks, 256, 0, c->stream>>>(d_y, count, c->prm.trunc_factor, (double *)c->d_gpart,
                                             c->d_counters + CNT_ENERGY, c->d_scal);
+    prof_end(c, KID_ENERGY);
     return cudaGetLastError();
 }
 
@@ -284,17 +292,22 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
     const float sy = (float)(1.0 / sqrt((double)c->ny));
     const unsigned rb = (unsigned)((total_rows + 3) / 4);
     if (total_rows > 0) {
-        DISPATCH_P(c->px, (k_init_rows<P_><<<rb, 256, 0, c->stream>>>(d_y, c->d_T, total_rows, c->d_scal,
-                                                                       c->d_twx, sx)));
+        DISPATCH_P(c->px, {
+            prof_begin(c, KID_INIT_ROWS);
+            k_init_rows<P_><<<rb, 256, 0, c->stream>>>(d_y, c->d_T, total_rows, c->d_scal, c->d_twx, sx);
+            prof_end(c, KID_INIT_ROWS);
+        });
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)c->ny * (1 + 2 * TXI + 1 + TXI) * sizeof(float2);
     dim3 grid(c->nx / TXI, c->q);
     DISPATCH_P(c->py, {
+        prof_begin(c, KID_INIT_COLS);
         k_init_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowidx, c->d_lineptr,
                                                         c->d_scal, c->d_Z, c->d_X0, c->nx, c->q, c->nc,
                                                         c->d_twy, sy);
+        prof_end(c, KID_INIT_COLS);
     });
     return cudaGetLastError();
 }
@@ -418,13 +431,17 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     if ((size_t)blocks * np > c->gpart_cap) blocks = (int)(c->gpart_cap / np);
     const size_t smem = (size_t)GRAM_CHUNK * q * sizeof(float2) + (size_t)np * sizeof(short2);
     double *gram = c->d_gram;
+    prof_begin(c, KID_GRAM_X0);
     k_gram_x0<<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart, c->d_counters + CNT_GRAMX0,
                                                          gram);
+    prof_end(c, KID_GRAM_X0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem2 = (size_t)q * q * sizeof(float2);
+    prof_begin(c, KID_EIG);
     k_eig<<<1, 256, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
                                         c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status);
+    prof_end(c, KID_EIG);
     return cudaGetLastError();
 }
 
@@ -452,8 +469,10 @@ __global__ void k_u0(const float2 *__restrict__ X0, const float2 *__restrict__ V
 
 cudaError_t launch_u0(lrccs_ctx *c) {
     const size_t smem = (size_t)c->q * c->r * sizeof(float2);
+    prof_begin(c, KID_U0);
     k_u0<<<304, 256, smem, c->stream>>>(c->d_X0, c->d_V, c->d_meta + MT_COUNT, c->d_sigma, c->n, c->q, c->r,
                                         c->d_Up);
+    prof_end(c, KID_U0);
     return cudaGetLastError();
 }
 

@@ -661,13 +661,19 @@ __global__ void __launch_bounds__(256) k_apply(float2 *__restrict__ U, float2 *_
 
 cudaError_t launch_qr(lrccs_ctx *c, int from_grad) {
     const int r = c->r;
+    prof_begin(c, KID_GD_GRAM);
     k_gd_gram<<<c->nblk, 256, 0, c->stream>>>(c->d_U, c->d_G, c->d_Up, c->d_scal, c->d_gpart,
                                                c->d_counters + CNT_QR1, c->d_R1inv, c->d_status, c->n, r, from_grad);
+    prof_end(c, KID_GD_GRAM);
+    prof_begin(c, KID_RINV_GRAM);
     k_rinv_gram<<<c->nblk, 256, 0, c->stream>>>(c->d_Up, c->d_R1inv, c->d_gpart, c->d_counters + CNT_QR2, c->d_M,
                                                  c->d_status, c->n, r);
+    prof_end(c, KID_RINV_GRAM);
     const size_t smem = (size_t)QCH * (3 * RMAXC + c->q) * sizeof(float2);
+    prof_begin(c, KID_APPLY);
     k_apply<<<c->nblk, 256, smem, c->stream>>>(c->d_U, c->d_Uprev, c->d_Up, c->d_M, c->d_Z, c->d_Hpart, c->d_gpart,
                                                c->d_counters + CNT_APPLY, c->d_scal, c->n, r, c->q, from_grad);
+    prof_end(c, KID_APPLY);
     return cudaGetLastError();
 }
 
@@ -690,8 +696,10 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
         const size_t smem = ((size_t)ny + (size_t)ny * TP) * sizeof(float2);
         dim3 grid(nx / tx, c->nc);
         DISPATCH_P(c->py, {
+            prof_begin(c, KID_FWD_COLS);
             k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_U, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
                                                            c->d_twy, sy);
+            prof_end(c, KID_FWD_COLS);
         });
     }
     // B
@@ -701,29 +709,37 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
         const int cpg = (c->nc + c->ncg - 1) / c->ncg;
         dim3 grid(c->n_used, c->ncg);
         DISPATCH_P(c->px, {
+            prof_begin(c, KID_FWD_ROWS);
             k_fwd_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, ny, r, c->nc, cpg,
                                                            c->d_twx, sx);
+            prof_end(c, KID_FWD_ROWS);
         });
     }
     // C
+    prof_begin(c, KID_SOLVE);
     k_solve<<<c->q, 64, 0, c->stream>>>(c->d_P, c->d_Hpart, c->d_lineptr, c->d_framerows, ny, r, c->q, c->ncg,
                                         c->nblk, c->d_B, c->d_status);
+    prof_end(c, KID_SOLVE);
     // D
     {
         const size_t smem = ((size_t)nx + RMAXC * RMAXC + (size_t)nx * RP) * sizeof(float2);
         dim3 grid(c->n_used, c->nc);
         DISPATCH_P(c->px, {
+            prof_begin(c, KID_ADJ_ROWS);
             k_adj_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist,
                                                            ny, r, c->d_twx, sx);
+            prof_end(c, KID_ADJ_ROWS);
         });
     }
     // E
     {
         const size_t smem = ((size_t)ny + (size_t)ny * RP + ny + (size_t)c->q * r) * sizeof(float2);
         DISPATCH_P(c->py, {
+            prof_begin(c, KID_ADJ_COLS);
             k_adj_cols<P_><<<nx, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowused, c->d_Z, c->d_B, c->d_G,
                                                          c->d_gpart, c->d_counters + CNT_GRAD, c->d_scal, nx, r,
                                                          c->q, c->nc, c->prm.eta_c, c->d_twy, sy);
+            prof_end(c, KID_ADJ_COLS);
         });
     }
     cudaError_t e = cudaGetLastError();
@@ -744,7 +760,9 @@ __global__ void k_images(const float2 *__restrict__ Uprev, const float2 *__restr
 }
 
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X) {
+    prof_begin(c, KID_IMAGES);
     k_images<<<608, 256, 0, c->stream>>>(c->d_Uprev, c->d_B, d_X, c->n, c->q, c->r);
+    prof_end(c, KID_IMAGES);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,10 @@ class IterInfo(C.Structure):
                 ("gnorm", C.c_double)]
 
 
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("timed", C.c_int64), ("ms", C.c_double)]
+
+
 _vp = C.c_void_p
 _st = C.c_int
 _sig = {
@@ -52,6 +56,9 @@ _sig = {
     "lrccs_get_images": (_st, [_vp, _vp]),
     "lrccs_get_buffer": (_st, [_vp, C.c_int, _vp, C.c_size_t]),
     "lrccs_synchronize": (_st, [_vp]),
+    "lrccs_profile": (_st, [_vp, C.c_char_p]),
+    "lrccs_profile_read": (_st, [_vp, C.POINTER(KernelStat), C.c_int32, C.POINTER(C.c_int32)]),
+    "lrccs_profile_reset": (_st, [_vp]),
     "lrccs_destroy": (None, [_vp]),
     "lrccs_last_error": (C.c_char_p, [_vp]),
     "lrccs_status_string": (C.c_char_p, [_st]),
@@ -135,6 +142,25 @@ def lrccs_synchronize(ctx):
 
 def lrccs_destroy(ctx):
     _lib.lrccs_destroy(ctx)
+
+
+def lrccs_profile(ctx, pattern):
+    """Time every later launch of the kernels whose name contains `pattern`
+    ("*" = all, None = none) with CUDA events on the context's stream."""
+    _check(ctx, _lib.lrccs_profile(ctx, None if pattern is None else pattern.encode()))
+
+
+def lrccs_profile_read(ctx):
+    """Synchronise and return [{name, launches, timed, ms}] for every kernel."""
+    buf = (KernelStat * 64)()
+    n = C.c_int32(0)
+    _check(ctx, _lib.lrccs_profile_read(ctx, buf, 64, C.byref(n)))
+    return [dict(name=buf[i].name.decode(), launches=buf[i].launches, timed=buf[i].timed, ms=buf[i].ms)
+            for i in range(n.value)]
+
+
+def lrccs_profile_reset(ctx):
+    _check(ctx, _lib.lrccs_profile_reset(ctx))
 
 
 def lrccs_last_error(ctx=None) -> str:
