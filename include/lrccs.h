@@ -162,6 +162,34 @@ lrccs_status lrccs_profile(lrccs_ctx *ctx, const char *pattern);
 lrccs_status lrccs_profile_read(lrccs_ctx *ctx, lrccs_kernel_stat *out, int32_t max, int32_t *count);
 lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
 
+/* Allocation-free truncation threshold.  The paper has no counterpart: this
+ * entry point exists for callers of this library that cannot call cudaMalloc,
+ * for example a reconstruction service that reserves all of its device
+ * memory when it starts and forbids allocation on the acquisition path, or a
+ * process whose device memory is owned by another allocator (a framework's
+ * caching pool) so that a direct cudaMalloc could fail or fragment it.
+ *
+ * Computes, on cuda_stream, the threshold of the spectral initialisation
+ *     *d_gamma = trunc_factor * sum_i |y_i|^2 / count
+ * over `count` complex64 entries at d_y (device memory), with |y_i|^2 formed
+ * in FP64 exactly as lrccs_init does; the result is the value lrccs_init uses
+ * up to the order of the FP64 summation.  d_gamma is a device float64.
+ *
+ * It allocates nothing and calls no allocating routine.  Its scratch is a
+ * fixed array in device memory at file scope (one FP64 partial sum per 65,536
+ * entries, 4,096 at most, plus a counter: 32 KiB + 256 B) that every device
+ * which loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address with the device current (a
+ * cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  Every call shares the array and clears its counter before
+ * use; calls whose work overlaps on the GPU (different streams, or another
+ * host thread) race on it and must be serialised by the caller.
+ * Errors: LRCCS_E_INVALID for null pointers or count outside
+ * [1, LRCCS_NOALLOC_MAX_ENTRIES]; LRCCS_E_CUDA; text in lrccs_last_error(NULL). */
+#define LRCCS_NOALLOC_MAX_ENTRIES ((int64_t)268435456)
+lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor, double *d_gamma,
+                                           void *cuda_stream);
+
 /* Wait for the context's stream and return any device-side failure. */
 lrccs_status lrccs_synchronize(lrccs_ctx *ctx);
 

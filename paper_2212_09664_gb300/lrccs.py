@@ -59,6 +59,7 @@ _sig = {
     "lrccs_profile": (_st, [_vp, C.c_char_p]),
     "lrccs_profile_read": (_st, [_vp, C.POINTER(KernelStat), C.c_int32, C.POINTER(C.c_int32)]),
     "lrccs_profile_reset": (_st, [_vp]),
+    "lrccs_trunc_threshold_noalloc": (_st, [_vp, C.c_int64, C.c_double, _vp, _vp]),
     "lrccs_destroy": (None, [_vp]),
     "lrccs_last_error": (C.c_char_p, [_vp]),
     "lrccs_status_string": (C.c_char_p, [_st]),
@@ -161,6 +162,15 @@ def lrccs_profile_read(ctx):
 
 def lrccs_profile_reset(ctx):
     _check(ctx, _lib.lrccs_profile_reset(ctx))
+
+
+def lrccs_trunc_threshold_noalloc(y, count, trunc_factor, gamma_out, stream=None):
+    """gamma = trunc_factor * sum |y_i|^2 / count into gamma_out (a CUDA float64
+    tensor), computed without any device allocation (for callers that reserve
+    their device memory up front and may not allocate).  The scratch is a fixed
+    array inside the library shared by all calls: do not overlap calls on the GPU."""
+    s = None if stream is None else _vp(stream.cuda_stream)
+    _check(None, _lib.lrccs_trunc_threshold_noalloc(_ptr(y), int(count), float(trunc_factor), _ptr(gamma_out), s))
 
 
 def lrccs_last_error(ctx=None) -> str:
