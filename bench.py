@@ -78,7 +78,7 @@ def iteration_bytes(p, r, n_used):
 
 def source_sha():
     h = hashlib.sha256()
-    for f in ("kernels_iter.cu", "common.cuh"):
+    for f in ("kernels_iter.cu", "kernels_small.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2212_09664_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -24,6 +24,7 @@ void set_err(lrccs_ctx *c, const char *fmt, ...) {
 
 cudaError_t configure_kernels_init(int max_smem);
 cudaError_t configure_kernels_iter(int max_smem);
+cudaError_t configure_kernels_small(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -116,9 +117,9 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     c->rmax = rmax;
     c->px = d.nx / 32;
     c->py = d.ny / 32;
-    c->ncg = d.ncoil >= 4 ? 2 : 1;
+    c->ncg = d.ncoil;   // one coil per CTA in the forward row pass: row Grams are kept per coil
     int nblk = (c->n + 127) / 128;
-    if (nblk > 296) nblk = 296;
+    if (nblk > 152) nblk = 152;
     c->nblk = nblk;
     const int n = c->n, q = c->q, nc = c->nc, ny = c->ny;
     const int npm = rmax * (rmax + 1) / 2;
@@ -156,6 +157,7 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     c->dev_smem_optin = optin;
     cudaError_t e = configure_kernels_init(optin);
     if (e == cudaSuccess) e = configure_kernels_iter(optin);
+    if (e == cudaSuccess) e = configure_kernels_small(optin);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream);

@@ -51,80 +51,6 @@ LRCCS_DEV int pair_index(int a, int b, int r) {  // a <= b
     return a * r - (a * (a - 1)) / 2 + (b - a);
 }
 
-// ---------------------------------------------------------------- warp FFT
-//
-// One warp computes one length-N DFT, N = 32 P (P = 1..8), as a Cooley-Tukey
-// split N = 32 x P: a P-point DFT inside each lane, a twiddle, then a 32-point
-// radix-2 decimation-in-time DFT across the lanes with warp shuffles.
-//   input : lane L holds v[m] = x[brev5(L) + 32 m]
-//   output: lane L holds v[k2] = X[k2 + P L]
-// tw: table of w_N^t = exp(-2 pi i t / N), t in [0, N) (shared memory);
-// inverse = true uses conjugate twiddles (unnormalised: the caller scales).
-
-template <int P>
-LRCCS_DEV void warp_fft(float2 (&v)[P], const float2 *__restrict__ tw, bool inverse) {
-    constexpr int N = 32 * P;
-    const int lane = threadIdx.x & 31;
-    const int n1 = brev5(lane);
-    const float sg = inverse ? -1.f : 1.f;
-    // 1) P-point DFT in registers: Y[k2] = sum_m v[m] w_P^{m k2}, w_P = w_N^32
-    if (P > 1) {
-        float2 y[P];
-#pragma unroll
-        for (int k2 = 0; k2 < P; ++k2) {
-            float2 acc = v[0];
-#pragma unroll
-            for (int m = 1; m < P; ++m) {
-                float2 w = tw[(32 * ((m * k2) % P)) % N];
-                w.y *= sg;
-                cfma(acc, v[m], w);
-            }
-            y[k2] = acc;
-        }
-        // 2) twiddle w_N^{n1 k2}
-#pragma unroll
-        for (int k2 = 0; k2 < P; ++k2) {
-            float2 w = tw[(n1 * k2) % N];
-            w.y *= sg;
-            v[k2] = (k2 == 0) ? y[0] : cmul(y[k2], w);
-        }
-    }
-    // 3) 32-point DIT across lanes (bit-reversed input, natural output)
-#pragma unroll
-    for (int h = 1; h < 32; h <<= 1) {
-        const int j = lane & (h - 1);
-        float2 w = tw[(j * (N / (2 * h))) % N];
-        w.y *= sg;
-        const bool top = (lane & h) == 0;
-#pragma unroll
-        for (int k2 = 0; k2 < P; ++k2) {
-            float2 u = shfl_xor2(v[k2], h);
-            v[k2] = top ? cadd(v[k2], cmul(w, u)) : csub(u, cmul(w, v[k2]));
-        }
-    }
-}
-
-// Run the transforms of a shared-memory tile: element e of transform t lives
-// at tile[e * es + t * ts].  Warp w handles transforms w, w + nwarps, ...
-// Results are written back in place, in natural order, scaled by `scale`.
-template <int P>
-LRCCS_DEV void tile_fft(float2 *tile, int es, int ts, int ntrans, const float2 *tw, bool inverse, float scale) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int n1 = brev5(lane);
-    for (int t = warp; t < ntrans; t += nw) {
-        float2 v[P];
-#pragma unroll
-        for (int m = 0; m < P; ++m) v[m] = tile[(n1 + 32 * m) * es + t * ts];
-        warp_fft<P>(v, tw, inverse);
-        __syncwarp();
-#pragma unroll
-        for (int k2 = 0; k2 < P; ++k2) tile[(k2 + P * lane) * es + t * ts] = cscale(v[k2], scale);
-        __syncwarp();
-    }
-}
-
 // Load the twiddle table of length N into shared memory.
 LRCCS_DEV void load_twiddles(float2 *s_tw, const float2 *g_tw, int N) {
     for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = g_tw[t];
@@ -158,10 +84,13 @@ LRCCS_DEV bool last_block_arrive(unsigned int *counter) {
 // removes the phase of a_pq and applies the real 2x2 Jacobi rotation:
 // G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]], A <- G^H A G, V <- V G.
 // V (ldv columns, may be global memory) is updated when non-null.
-__device__ inline void block_jacobi(float2 *A, int n, float2 *V, int ldv, float *s_c, float *s_s, float2 *s_e,
-                             int *s_cnt, int max_sweeps) {
+// A rotation is skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|) or |a_pq| <= abs_tol;
+// the sweeps stop when a whole sweep skips every rotation.
+__device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ldv, float *s_c, float *s_s, float2 *s_e,
+                             int *s_cnt, int max_sweeps, float abs_tol = 0.f) {
     const int n2 = n + (n & 1);
     const int npair = n2 / 2;
+    __shared__ short s_pp[64], s_qq[64];   // the pairs of the current round
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *s_cnt = 0;
         __syncthreads();
@@ -170,13 +99,15 @@ __device__ inline void block_jacobi(float2 *A, int n, float2 *V, int ldv, float 
                 int p, qq;
                 if (i == 0) { p = rnd; qq = n2 - 1; }
                 else { p = (rnd + i) % (n2 - 1); qq = (rnd - i + n2 - 1) % (n2 - 1); }
+                s_pp[i] = (short)p;
+                s_qq[i] = (short)qq;
                 float c = 1.f, s = 0.f;
                 float2 e = make_float2(1.f, 0.f);
                 if (p < n && qq < n) {
-                    const float2 apq = A[p * n + qq];
+                    const float2 apq = A[p * lda + qq];
                     const float b = hypotf(apq.x, apq.y);
-                    const float al = A[p * n + p].x, ga = A[qq * n + qq].x;
-                    if (b > 1e-30f && b > 1e-7f * sqrtf(fabsf(al) * fabsf(ga))) {
+                    const float al = A[p * lda + p].x, ga = A[qq * lda + qq].x;
+                    if (b > 1e-30f && b > abs_tol && b > 1e-7f * sqrtf(fabsf(al) * fabsf(ga))) {
                         e = make_float2(apq.x / b, apq.y / b);
                         const float tau = (ga - al) / (2.f * b);
                         const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
@@ -192,33 +123,29 @@ __device__ inline void block_jacobi(float2 *A, int n, float2 *V, int ldv, float 
             __syncthreads();
             // rows p, q: A <- G^H A
             for (int task = threadIdx.x; task < npair * n; task += blockDim.x) {
-                const int i = task / n, m = task % n;
+                const int i = task / n, m = task - i * n;
                 if (s_s[i] == 0.f) continue;
-                int p, qq;
-                if (i == 0) { p = rnd; qq = n2 - 1; }
-                else { p = (rnd + i) % (n2 - 1); qq = (rnd - i + n2 - 1) % (n2 - 1); }
+                const int p = s_pp[i], qq = s_qq[i];
                 const float c = s_c[i], s = s_s[i];
                 const float2 e = s_e[i];
-                const float2 ap = A[p * n + m], aq = A[qq * n + m];
+                const float2 ap = A[p * lda + m], aq = A[qq * lda + m];
                 const float2 eaq = cmul(e, aq);
-                A[p * n + m] = make_float2(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-                A[qq * n + m] = make_float2(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
+                A[p * lda + m] = make_float2(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
+                A[qq * lda + m] = make_float2(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
             }
             __syncthreads();
             // columns p, q: A <- A G ; V <- V G
             for (int task = threadIdx.x; task < npair * n; task += blockDim.x) {
-                const int i = task / n, m = task % n;
+                const int i = task / n, m = task - i * n;
                 if (s_s[i] == 0.f) continue;
-                int p, qq;
-                if (i == 0) { p = rnd; qq = n2 - 1; }
-                else { p = (rnd + i) % (n2 - 1); qq = (rnd - i + n2 - 1) % (n2 - 1); }
+                const int p = s_pp[i], qq = s_qq[i];
                 const float c = s_c[i], s = s_s[i];
                 const float2 eh = cconj(s_e[i]);
                 {
-                    const float2 ap = A[m * n + p], aq = A[m * n + qq];
+                    const float2 ap = A[m * lda + p], aq = A[m * lda + qq];
                     const float2 e2 = cmul(eh, aq);
-                    A[m * n + p] = make_float2(c * ap.x - s * e2.x, c * ap.y - s * e2.y);
-                    A[m * n + qq] = make_float2(s * ap.x + c * e2.x, s * ap.y + c * e2.y);
+                    A[m * lda + p] = make_float2(c * ap.x - s * e2.x, c * ap.y - s * e2.y);
+                    A[m * lda + qq] = make_float2(s * ap.x + c * e2.x, s * ap.y + c * e2.y);
                 }
                 if (V) {
                     const float2 vp = V[m * ldv + p], vq = V[m * ldv + qq];
@@ -244,4 +171,263 @@ static inline cudaError_t allow_smem(K kernel, int optin) {
     cudaError_t e = cudaFuncGetAttributes(&a, kernel);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+}
+
+// ---------------------------------------------------------------- warp-level FP64 small linear algebra
+// For the r x r (r <= 32) Hermitian systems of the B-step and of CholeskyQR2.
+// Matrices are FP64 (re, im) pairs, row-major, in shared memory; one full warp
+// calls each routine.  GB300's FP64 pipe is narrow, so the work is spread over
+// the lanes instead of running on one thread.
+
+LRCCS_DEV double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;  // identical in every lane (each level adds the same two numbers)
+}
+
+// In place A = L L^H: the lower triangle of A receives L (real positive
+// diagonal).  Returns false (in every lane) if A is not positive definite.
+LRCCS_DEV bool warp_cholesky(double *A, int r) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < r; ++c) {
+        double part = 0.0;
+        if (lane < c) {
+            const double ar = A[(c * r + lane) * 2], ai = A[(c * r + lane) * 2 + 1];
+            part = ar * ar + ai * ai;
+        }
+        part = warp_sum_d(part);
+        double d = A[(c * r + c) * 2] - part;
+        if (!(d > 0.0)) return false;
+        d = sqrt(d);
+        __syncwarp();
+        if (lane > c && lane < r) {
+            double vr = A[(lane * r + c) * 2], vi = A[(lane * r + c) * 2 + 1];
+            for (int m = 0; m < c; ++m) {  // v -= L[lane][m] conj(L[c][m])
+                const double ar = A[(lane * r + m) * 2], ai = A[(lane * r + m) * 2 + 1];
+                const double br = A[(c * r + m) * 2], bi = A[(c * r + m) * 2 + 1];
+                vr -= ar * br + ai * bi;
+                vi -= ai * br - ar * bi;
+            }
+            A[(lane * r + c) * 2] = vr / d;
+            A[(lane * r + c) * 2 + 1] = vi / d;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            A[(c * r + c) * 2] = d;
+            A[(c * r + c) * 2 + 1] = 0.0;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Rinv = (L^H)^{-1} (upper triangular) from the lower factor L in A.
+// Li: r * r * 2 doubles of shared scratch.  Lane j computes column j of L^{-1}.
+LRCCS_DEV void warp_rinv(const double *A, int r, double *Li, double *Rinv) {
+    const int lane = threadIdx.x & 31;
+    if (lane < r) {
+        const int j = lane;
+        for (int i = 0; i < j; ++i) {
+            Li[(i * r + j) * 2] = 0.0;
+            Li[(i * r + j) * 2 + 1] = 0.0;
+        }
+        Li[(j * r + j) * 2] = 1.0 / A[(j * r + j) * 2];
+        Li[(j * r + j) * 2 + 1] = 0.0;
+        for (int i = j + 1; i < r; ++i) {
+            double vr = 0.0, vi = 0.0;
+            for (int m = j; m < i; ++m) {
+                const double ar = A[(i * r + m) * 2], ai = A[(i * r + m) * 2 + 1];
+                const double br = Li[(m * r + j) * 2], bi = Li[(m * r + j) * 2 + 1];
+                vr += ar * br - ai * bi;
+                vi += ar * bi + ai * br;
+            }
+            const double d = A[(i * r + i) * 2];
+            Li[(i * r + j) * 2] = -vr / d;
+            Li[(i * r + j) * 2 + 1] = -vi / d;
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < r * r; e += 32) {
+        const int a = e / r, b = e - a * r;
+        Rinv[e * 2] = Li[(b * r + a) * 2];
+        Rinv[e * 2 + 1] = -Li[(b * r + a) * 2 + 1];
+    }
+    __syncwarp();
+}
+
+// Solve L L^H x = h (L lower in A); h and x are r (re, im) pairs in shared memory.
+LRCCS_DEV void warp_chol_solve(const double *A, int r, const double *h, double *x) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < r; ++c) {  // L z = h
+        double pr = 0.0, pi = 0.0;
+        if (lane < c) {
+            const double ar = A[(c * r + lane) * 2], ai = A[(c * r + lane) * 2 + 1];
+            const double zr = x[2 * lane], zi = x[2 * lane + 1];
+            pr = ar * zr - ai * zi;
+            pi = ar * zi + ai * zr;
+        }
+        pr = warp_sum_d(pr);
+        pi = warp_sum_d(pi);
+        const double d = A[(c * r + c) * 2];
+        if (lane == 0) {
+            x[2 * c] = (h[2 * c] - pr) / d;
+            x[2 * c + 1] = (h[2 * c + 1] - pi) / d;
+        }
+        __syncwarp();
+    }
+    for (int c = r - 1; c >= 0; --c) {  // L^H x = z
+        double pr = 0.0, pi = 0.0;
+        if (lane > c && lane < r) {  // conj(L[lane][c]) x[lane]
+            const double ar = A[(lane * r + c) * 2], ai = -A[(lane * r + c) * 2 + 1];
+            const double zr = x[2 * lane], zi = x[2 * lane + 1];
+            pr = ar * zr - ai * zi;
+            pi = ar * zi + ai * zr;
+        }
+        pr = warp_sum_d(pr);
+        pi = warp_sum_d(pi);
+        const double d = A[(c * r + c) * 2];
+        __syncwarp();
+        if (lane == 0) {
+            x[2 * c] = (x[2 * c] - pr) / d;
+            x[2 * c + 1] = (x[2 * c + 1] - pi) / d;
+        }
+        __syncwarp();
+    }
+}
+
+// Sum nblk rows of float2 partials (row length len, row b at part + b * len)
+// in FP64 into dst (re, im pairs), entry e by warp e mod nwarps, lanes over
+// rows in a fixed order: deterministic.  All threads of the block call it.
+LRCCS_DEV void block_reduce_rows(const float2 *part, int nblk, int len, double *dst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = warp; e < len; e += nw) {
+        double re = 0.0, im = 0.0;
+        for (int b = lane; b < nblk; b += 32) {
+            const float2 v = __ldcg(part + (size_t)b * len + e);
+            re += v.x;
+            im += v.y;
+        }
+        re = warp_sum_d(re);
+        im = warp_sum_d(im);
+        if (lane == 0) {
+            dst[2 * e] = re;
+            dst[2 * e + 1] = im;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- asynchronous global -> shared copies
+// cp.async keeps many copies in flight per thread without staging through
+// registers; cp_async_wait() waits for all of this thread's copies, after
+// which a __syncthreads() publishes the tile to the block.
+
+LRCCS_DEV unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// 8-byte copy (one complex64); src must be 8-byte aligned.
+LRCCS_DEV void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// 16-byte copy (two complex64); src and dst must be 16-byte aligned.
+LRCCS_DEV void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+LRCCS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+LRCCS_DEV void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// wait until at most one committed group is still pending (double buffering)
+LRCCS_DEV void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------- latency-lean FP64 r x r kernels
+// On this GPU a dependent FP64 FMA costs ~64 cycles and an FP64 square root or
+// division several hundred, so the r x r factorizations below avoid both: a
+// reciprocal square root / reciprocal is seeded in FP32 and refined by one
+// Newton step in FP64 (relative error ~1e-14), and every step spreads its
+// updates over the lanes of a warp (right-looking forms).
+
+LRCCS_DEV double d_rsqrt(double x) {   // 1/sqrt(x), x > 0
+    double y = (double)rsqrtf((float)x);
+    const double t = x * y * y;
+    return y * fma(-0.5, t, 1.5);
+}
+LRCCS_DEV double d_rcp(double x) {     // 1/x, x != 0
+    const double r = (double)__frcp_rn((float)x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// In place A = L L^H (A Hermitian, FP64 (re, im) pairs, row-major, r <= 32):
+// the lower triangle of A receives L and invd[c] = 1 / L[c][c].  One warp;
+// lane i owns row i of the trailing matrix.  Returns false if A is not
+// positive definite (same value in every lane).
+LRCCS_DEV bool warp_cholesky_rl(double *A, int r, double *invd) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < r; ++c) {
+        const double d = A[(c * r + c) * 2];
+        if (!(d > 0.0)) return false;
+        const double is = d_rsqrt(d);
+        // column c below the diagonal: L[i][c] = A[i][c] / sqrt(d)
+        double lr = 0.0, li = 0.0;
+        if (lane > c && lane < r) {
+            lr = A[(lane * r + c) * 2] * is;
+            li = A[(lane * r + c) * 2 + 1] * is;
+        }
+        __syncwarp();
+        if (lane == c) {
+            A[(c * r + c) * 2] = d * is;
+            A[(c * r + c) * 2 + 1] = 0.0;
+            invd[c] = is;
+        }
+        if (lane > c && lane < r) {
+            A[(lane * r + c) * 2] = lr;
+            A[(lane * r + c) * 2 + 1] = li;
+        }
+        __syncwarp();
+        // trailing update A[i][j] -= L[i][c] conj(L[j][c]) for c < j <= i, the
+        // (r-c-1)(r-c)/2 entries spread over the lanes
+        const int rt = r - c - 1;
+        for (int e = lane; e < rt * (rt + 1) / 2; e += 32) {
+            int a, b;
+            pair_of(e, rt, a, b);
+            const int j = c + 1 + a, i = c + 1 + b;
+            const double ar = A[(i * r + c) * 2], ai = A[(i * r + c) * 2 + 1];
+            const double br = A[(j * r + c) * 2], bi = A[(j * r + c) * 2 + 1];
+            A[(i * r + j) * 2] -= ar * br + ai * bi;
+            A[(i * r + j) * 2 + 1] -= ai * br - ar * bi;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Solve L L^H x = h with the factor of warp_cholesky_rl; h and x are r (re, im)
+// pairs in shared memory (h is consumed).  Right-looking substitutions.
+LRCCS_DEV void warp_chol_solve_rl(const double *L, const double *invd, int r, double *h, double *x) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < r; ++c) {            // L z = h  (z in h)
+        const double zr = h[2 * c] * invd[c], zi = h[2 * c + 1] * invd[c];
+        __syncwarp();
+        if (lane == c) {
+            h[2 * c] = zr;
+            h[2 * c + 1] = zi;
+        }
+        if (lane > c && lane < r) {          // h[i] -= L[i][c] z
+            const double ar = L[(lane * r + c) * 2], ai = L[(lane * r + c) * 2 + 1];
+            h[2 * lane] -= ar * zr - ai * zi;
+            h[2 * lane + 1] -= ar * zi + ai * zr;
+        }
+        __syncwarp();
+    }
+    for (int c = r - 1; c >= 0; --c) {       // L^H x = z
+        const double xr = h[2 * c] * invd[c], xi = h[2 * c + 1] * invd[c];
+        __syncwarp();
+        if (lane == c) {
+            x[2 * c] = xr;
+            x[2 * c + 1] = xi;
+        }
+        if (lane < c) {                      // z[i] -= conj(L[c][i]) x_c
+            const double ar = L[(c * r + lane) * 2], ai = -L[(c * r + lane) * 2 + 1];
+            h[2 * lane] -= ar * xr - ai * xi;
+            h[2 * lane + 1] -= ar * xi + ai * xr;
+        }
+        __syncwarp();
+    }
 }

@@ -122,6 +122,7 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);
 cudaError_t launch_u0(lrccs_ctx *c);
 cudaError_t launch_qr(lrccs_ctx *c, int from_grad);   // F, G, H kernels
+cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);
 int npairs_of(int r);

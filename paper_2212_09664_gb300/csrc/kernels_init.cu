@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fft.cuh"
 #include "internal.h"
 
 // ---------------------------------------------------------------- twiddles
@@ -183,27 +184,27 @@ template <int P>
 __global__ void __launch_bounds__(256) k_init_rows(const float2 *__restrict__ y, float2 *__restrict__ T0,
                                                     int64_t total_rows, const double *__restrict__ scal,
                                                     const float2 *__restrict__ g_tw, float scale) {
+    // 4 rows x {plain, truncated} = 8 transforms per block; tile[x][2 row + ch]
     constexpr int N = 32 * P;
+    constexpr int ROWS = 4, TPR = 2 * ROWS + 1;
     __shared__ float2 s_tw[N];
+    __shared__ float2 tile[N * TPR];
     load_twiddles(s_tw, g_tw, N);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * 4 + (warp >> 1);
-    const int ch = warp & 1;
-    if (g >= total_rows) return;
+    const int64_t g0 = (int64_t)blockIdx.x * ROWS;
     const double gam = scal[SC_GAMMA];
-    const float2 *yr = y + g * N;
-    const int n1 = brev5(lane);
-    float2 v[P];
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-        float2 a = yr[n1 + 32 * m];
-        if (ch == 1 && abs2_rn(a) > gam) a = make_float2(0.f, 0.f);
-        v[m] = a;
+    for (int e = threadIdx.x; e < ROWS * N; e += blockDim.x) {
+        const int row = e / N, x = e - row * N;
+        float2 a = make_float2(0.f, 0.f);
+        if (g0 + row < total_rows) a = y[(g0 + row) * N + x];
+        tile[x * TPR + 2 * row] = a;
+        tile[x * TPR + 2 * row + 1] = abs2_rn(a) > gam ? make_float2(0.f, 0.f) : a;
     }
-    warp_fft<P>(v, s_tw, true);
-#pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) T0[(g * N + k2 + P * lane) * 2 + ch] = cscale(v[k2], scale);
+    __syncthreads();
+    fft::tile_dft<N, true>(tile, TPR, 2 * ROWS, s_tw, scale);
+    for (int e = threadIdx.x; e < ROWS * 2 * N; e += blockDim.x) {
+        const int row = e / (2 * N), rem = e - row * 2 * N, x = rem >> 1, ch = rem & 1;
+        if (g0 + row < total_rows) T0[(g0 + row) * N * 2 + rem] = tile[x * TPR + 2 * row + ch];
+    }
 }
 
 #define TXI 8
@@ -221,16 +222,15 @@ __global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0
     float2 *s_S = tile + NY * TP;
     load_twiddles(s_tw, g_tw, NY);
     const int k = blockIdx.y, x0 = blockIdx.x * TXI;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n1 = brev5(lane);
     const int n = NY * nx;
     const int lp = lineptr[k];
     const int64_t mk = (int64_t)(lineptr[k + 1] - lp) * nx;
     const int64_t fbase = (int64_t)nc * lp * nx;
-    float2 acc[2][P];
+    // thread owns tile elements e = tid + 256 u: yy = e / (2 TXI), cc = e % (2 TXI)
+    constexpr int ACC = (NY * 2 * TXI + 255) / 256;
+    float2 acc[ACC];
 #pragma unroll
-    for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc[tt][m] = make_float2(0.f, 0.f);
+    for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
     for (int j = 0; j < nc; ++j) {
         __syncthreads();
         for (int e = threadIdx.x; e < NY * 2 * TXI; e += blockDim.x) {
@@ -243,32 +243,26 @@ __global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0
         for (int e = threadIdx.x; e < NY * TXI; e += blockDim.x)
             s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXI) * nx + x0 + (e % TXI)];
         __syncthreads();
+        fft::tile_dft<NY, true>(tile, TP, 2 * TXI, s_tw, scale);
 #pragma unroll
-        for (int tt = 0; tt < 2; ++tt) {
-            const int t = warp + 8 * tt;
-            float2 v[P];
-#pragma unroll
-            for (int m = 0; m < P; ++m) v[m] = tile[(n1 + 32 * m) * TP + t];
-            warp_fft<P>(v, s_tw, true);
-#pragma unroll
-            for (int k2 = 0; k2 < P; ++k2) {
-                const int yy = k2 + P * lane;
-                cfmac(acc[tt][k2], s_S[yy * TXI + (t >> 1)], cscale(v[k2], scale));
+        for (int u = 0; u < ACC; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            if (e < NY * 2 * TXI) {
+                const int yy = e / (2 * TXI), cc = e % (2 * TXI);
+                cfmac(acc[u], s_S[yy * TXI + (cc >> 1)], tile[yy * TP + cc]);
             }
         }
     }
     const double mbar = scal[SC_MBAR];
     const float xs = (mk > 0) ? (float)(1.0 / sqrt((double)mk * mbar)) : 0.f;
 #pragma unroll
-    for (int tt = 0; tt < 2; ++tt) {
-        const int t = warp + 8 * tt;
-        const int xx = t >> 1, ch = t & 1;
-#pragma unroll
-        for (int k2 = 0; k2 < P; ++k2) {
-            const int yy = k2 + P * lane;
-            const size_t i = (size_t)yy * nx + x0 + xx;
-            if (ch == 0) Z[i * q + k] = acc[tt][k2];
-            else X0[i * q + k] = cscale(acc[tt][k2], xs);
+    for (int u = 0; u < ACC; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        if (e < NY * 2 * TXI) {
+            const int yy = e / (2 * TXI), cc = e % (2 * TXI);
+            const size_t i = (size_t)yy * nx + x0 + (cc >> 1);
+            if ((cc & 1) == 0) Z[i * q + k] = acc[u];
+            else X0[i * q + k] = cscale(acc[u], xs);
         }
     }
 }
@@ -376,17 +370,39 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
 // the energy of the first floor(min(n, q, C min m_k)/10) (at least 1).
 __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int rank_in, int rmax,
                       double energy_pct, float2 *V, int32_t *order, double *sigma, int32_t *meta,
-                      unsigned int *status) {
-    extern __shared__ float2 sA[];  // q * q
+                      unsigned int *status, int v_in_smem) {
+    // A (and V when it fits) in shared memory with an odd row pitch, so that
+    // the column updates of the rotations hit distinct banks
+    extern __shared__ float2 sA[];
     __shared__ float s_c[64], s_s[64];
     __shared__ float2 s_e[64];
     __shared__ int s_cnt;
+    __shared__ double s_fro[32];
+    const int ld = q | 1;
+    float2 *Vw = v_in_smem ? sA + q * ld : V;
+    const int ldv = v_in_smem ? ld : q;
+    double fro = 0.0;
     for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-        sA[e] = make_float2((float)gram[2 * e], (float)gram[2 * e + 1]);
-        V[e] = make_float2((e / q) == (e % q) ? 1.f : 0.f, 0.f);
+        const int a = e / q, b = e - a * q;
+        sA[a * ld + b] = make_float2((float)gram[2 * e], (float)gram[2 * e + 1]);
+        Vw[a * ldv + b] = make_float2(a == b ? 1.f : 0.f, 0.f);
+        fro += gram[2 * e] * gram[2 * e] + gram[2 * e + 1] * gram[2 * e + 1];
     }
+    fro = warp_sum_d(fro);
+    if ((threadIdx.x & 31) == 0) s_fro[threadIdx.x >> 5] = fro;
     __syncthreads();
-    block_jacobi(sA, q, V, q, s_c, s_s, s_e, &s_cnt, 40);
+    fro = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fro += s_fro[w];
+    // off-diagonal entries below 1e-9 ||A||_F are under FP32 rounding of the
+    // largest entries; cyclic Jacobi converges quadratically, so 12 sweeps bound it
+    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 12, (float)(1e-9 * sqrt(fro)));
+    if (v_in_smem)
+        for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = Vw[(e / q) * ldv + e % q];
+    // diagonal to a compact array (the sort below reads sA[i * q + i])
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < q; ++i) sA[i * q + i] = sA[i * ld + i];
+    __syncthreads();
     if (threadIdx.x == 0) {
         // selection sort of the eigenvalue order, descending
         for (int i = 0; i < q; ++i) order[i] = i;
@@ -437,10 +453,12 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     prof_end(c, KID_GRAM_X0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem2 = (size_t)q * q * sizeof(float2);
+    const int ld = q | 1;
+    const int v_in_smem = (size_t)2 * q * ld * sizeof(float2) + 4096 <= (size_t)c->dev_smem_optin;
+    const size_t smem2 = (size_t)(v_in_smem ? 2 : 1) * q * ld * sizeof(float2);
     prof_begin(c, KID_EIG);
-    k_eig<<<1, 256, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
-                                        c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status);
+    k_eig<<<1, 1024, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
+                                        c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem);
     prof_end(c, KID_EIG);
     return cudaGetLastError();
 }
