@@ -34,7 +34,7 @@ T_ITER = 50
 METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
 UNIT = "frame-iterations/s"
 FLUSH_BYTES = 256 << 20            # > 129 MB L2
-ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_gd_gram",
+ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_grad",
                 "k_rinv_gram", "k_apply"]
 
 
@@ -63,10 +63,10 @@ def kernel_bytes(name, p, r, n_used):
         "k_fwd_cols": n * r + C * n + C * r * nu,        # read U, d_j; write F_y(d_j o U) on sampled rows
         "k_fwd_rows": 2 * C * r * nu,                    # read + write the sampled rows (in place)
         "k_adj_rows": 2 * C * r * nu,                    # read FU, write F_x^H(FU W)
-        "k_adj_cols": C * r * nu + C * n + n * q + n * r,  # read rows, d_j, Z; write grad
-        "k_gd_gram": 3 * n * r,                          # read U, grad; write U+
-        "k_rinv_gram": n * r,                            # read U+
-        "k_apply": 4 * n * r + n * q,                    # read U+, U, Z; write U, U_{t-1}
+        "k_adj_cols": C * r * nu + C * n + n * r,        # read rows, d_j; write sum_j conj(d_j) F^H K_j
+        "k_grad": 3 * n * r + n * q,                     # read that, U, Z; write grad
+        "k_rinv_gram": 2 * n * r,                        # read U, grad (U+ formed on the fly)
+        "k_apply": 4 * n * r + n * q,                    # read U, grad, Z; write U, U_{t-1}
         "k_solve": 0,
     }.get(name, 0)
     return 8 * b

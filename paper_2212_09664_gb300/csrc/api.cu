@@ -123,7 +123,7 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     c->nblk = nblk;
     const int n = c->n, q = c->q, nc = c->nc, ny = c->ny;
     const int npm = rmax * (rmax + 1) / 2;
-    size_t gcap = (size_t)nblk * rmax * rmax;
+    size_t gcap = (size_t)nblk * (2 * npm + rmax * rmax);   // k_grad's partial sums are the largest per block
     if ((size_t)c->nx * npm > gcap) gcap = (size_t)c->nx * npm;
     if ((size_t)152 * q * (q + 1) / 2 > gcap) gcap = (size_t)152 * q * (q + 1) / 2;
     if (gcap < 1024) gcap = 1024;
@@ -378,7 +378,7 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
     "k_eig", "k_u0", "k_gd_gram", "k_rinv_gram", "k_apply", "k_fwd_cols", "k_fwd_rows", "k_solve",
-    "k_adj_rows", "k_adj_cols", "k_images"};
+    "k_adj_rows", "k_adj_cols", "k_images", "k_grad"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

@@ -295,26 +295,96 @@ LRCCS_DEV void warp_chol_solve(const double *A, int r, const double *h, double *
     }
 }
 
-// Sum nblk rows of float2 partials (row length len, row b at part + b * len)
-// in FP64 into dst (re, im pairs), entry e by warp e mod nwarps, lanes over
-// rows in a fixed order: deterministic.  All threads of the block call it.
-LRCCS_DEV void block_reduce_rows(const float2 *part, int nblk, int len, double *dst) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int e = warp; e < len; e += nw) {
-        double re = 0.0, im = 0.0;
-        for (int b = lane; b < nblk; b += 32) {
-            const float2 v = __ldcg(part + (size_t)b * len + e);
-            re += v.x;
-            im += v.y;
+// Compensated FP32 summation (Knuth's two-sum): a (hi, lo) pair carries ~48
+// bits, at FP32 speed (an FP64 add is ~14x slower on this GPU).
+struct fsum2 {
+    float hi, lo;
+};
+LRCCS_DEV void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+LRCCS_DEV void fsum_add(fsum2 &acc, float x) {
+    float s, e;
+    two_sum(acc.hi, x, s, e);
+    acc.hi = s;
+    acc.lo += e;
+}
+// Warp-wide sum of (hi, lo) pairs; identical result in every lane.
+LRCCS_DEV double warp_fsum(fsum2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o), ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        float s, e;
+        // order the pair so that both lanes of a butterfly compute the same sum
+        const bool first = (threadIdx.x & o) == 0;
+        two_sum(first ? v.hi : oh, first ? oh : v.hi, s, e);
+        v.lo = (first ? v.lo + ol : ol + v.lo) + e;
+        v.hi = s;
+    }
+    return (double)v.hi + (double)v.lo;
+}
+
+// Block-wide compensated sums dst[e] = sum_{m < nitem} fetch(e, m) for
+// e < nent, written as FP64 (re, im) pairs.  Thread (entry e, slice s) sums
+// items s, s + S, s + 2S, ... in that order with RB loads in flight, and the S
+// slices are then combined in order: deterministic, and one memory latency per
+// RB items instead of one per item.  All threads of the block (at most 256)
+// call it; it ends with a barrier.
+template <class F>
+LRCCS_DEV void block_sum(int nent, int nitem, double *dst, F fetch) {
+    constexpr int RB = 16;
+    __shared__ float4 s_acc[256];   // (hi, lo) of re and im per thread
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int S = nent >= nt ? 1 : max(1, min(nt / nent, nitem));
+    for (int base = 0; base < nent; base += nt) {
+        const int e = base + (S == 1 ? t : t % nent), s = S == 1 ? 0 : t / nent;
+        fsum2 re = {0.f, 0.f}, im = {0.f, 0.f};
+        if (e < nent && s < S) {
+            for (int m = s; m < nitem; m += S * RB) {
+                float2 v[RB];
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int mm = m + u * S;
+                    v[u] = mm < nitem ? fetch(e, mm) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    fsum_add(re, v[u].x);
+                    fsum_add(im, v[u].y);
+                }
+            }
         }
-        re = warp_sum_d(re);
-        im = warp_sum_d(im);
-        if (lane == 0) {
-            dst[2 * e] = re;
-            dst[2 * e + 1] = im;
+        if (S == 1) {
+            if (e < nent) {
+                dst[2 * e] = (double)re.hi + (double)re.lo;
+                dst[2 * e + 1] = (double)im.hi + (double)im.lo;
+            }
+            continue;
+        }
+        s_acc[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        __syncthreads();
+        if (t < nent) {
+            fsum2 R = {0.f, 0.f}, I = {0.f, 0.f};
+            for (int ss = 0; ss < S; ++ss) {
+                const float4 a = s_acc[ss * nent + t];
+                fsum_add(R, a.x);
+                R.lo += a.y;
+                fsum_add(I, a.z);
+                I.lo += a.w;
+            }
+            dst[2 * t] = (double)R.hi + (double)R.lo;
+            dst[2 * t + 1] = (double)I.hi + (double)I.lo;
         }
     }
     __syncthreads();
+}
+
+// Sum nblk rows of float2 partials (row length len, row b at part + b * len)
+// into dst (FP64 re, im pairs).
+LRCCS_DEV void block_reduce_rows(const float2 *part, int nblk, int len, double *dst) {
+    block_sum(len, nblk, dst, [=](int e, int b) { return __ldcg(part + (size_t)b * len + e); });
 }
 
 // ---------------------------------------------------------------- asynchronous global -> shared copies

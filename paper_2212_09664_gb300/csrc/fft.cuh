@@ -230,9 +230,12 @@ template <int N, bool INV>
 LRCCS_DEV void tile_dft(float2 *tile, int es, int ntrans, const float2 *__restrict__ tw, float scale) {
     constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // pass 1: DFT_R1 over m of x[j2 + R2 m], times w_N^{j2 k1}
-    for (int it = tid; it < ntrans * R2; it += nthr) {
-        const int t = it % ntrans, j2 = it / ntrans;
+    // pass 1: DFT_R1 over m of x[j2 + R2 m], times w_N^{j2 k1}.  Requires
+    // ntrans <= blockDim.x: thread -> transform t = tid % ntrans (fixed) and
+    // j2 = tid / ntrans, stepping by the number of thread groups.
+    const int ngrp = nthr / ntrans;
+    const int t = tid % ntrans, g0 = tid / ntrans;
+    for (int j2 = (g0 < ngrp ? g0 : R2); j2 < R2; j2 += ngrp) {
         float2 v[R1];
 #pragma unroll
         for (int m = 0; m < R1; ++m) v[m] = tile[(j2 + R2 * m) * es + t];

@@ -37,7 +37,7 @@ enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_GRAD, CNT_QR1, CNT_QR2, CNT_APPLY, CNT_CO
 enum {
     KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
     KID_EIG, KID_U0, KID_GD_GRAM, KID_RINV_GRAM, KID_APPLY, KID_FWD_COLS, KID_FWD_ROWS, KID_SOLVE,
-    KID_ADJ_ROWS, KID_ADJ_COLS, KID_IMAGES, KID_COUNT
+    KID_ADJ_ROWS, KID_ADJ_COLS, KID_IMAGES, KID_GRAD, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -121,7 +121,8 @@ cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);
 cudaError_t launch_u0(lrccs_ctx *c);
-cudaError_t launch_qr(lrccs_ctx *c, int from_grad);   // F, G, H kernels
+cudaError_t launch_grad(lrccs_ctx *c);                 // F kernel (iteration)
+cudaError_t launch_qr(lrccs_ctx *c, int from_grad);   // F (init), G, H kernels
 cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);

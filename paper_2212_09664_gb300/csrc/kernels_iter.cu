@@ -16,8 +16,9 @@
 //   B k_fwd_rows  : F_x of every sampled row of one coil, row Gram -> FU (in place), P[j][ky]
 //   C k_solve     : G_k = sum of its rows' P, h_k, FP64 Cholesky    -> B
 //   D k_adj_rows  : K = FU W_ky, F_x^H                              -> T (in place)
-//   E k_adj_cols  : F_y^H, conj(d_j) coil sum, - Z B^H              -> grad; eta at t = 1
-//   F-H           : GD step and CholeskyQR2
+//   E k_adj_cols  : F_y^H, conj(d_j) coil sum                      -> Gk
+//   F k_grad      : grad = Gk - Z B^H, Grams, eta (t = 1), R1      (kernels_small.cu)
+//   G, H          : CholeskyQR2 of U - eta grad                    (kernels_small.cu)
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
 #include <math.h>
@@ -189,30 +190,16 @@ __global__ void __launch_bounds__(256) k_adj_rows(float2 *__restrict__ T, const 
 }
 
 // ---------------------------------------------------------------- E: adjoint, along y + coil sum
+// Gk = sum_j conj(d_j) o F_y^H (column x of coil j's row-transformed K_j);
+// the - Z B^H term and the Grams are added by k_grad (kernels_small.cu).
 
-// Stage column x of coil j: rows ky with rowused[ky] by cp.async, the other
-// rows set to zero (the buffer holds the previous coil's in-place transform).
-template <int NY>
-LRCCS_DEV void stage_column(float2 *tile, float2 *sS, const float2 *__restrict__ T, const float2 *__restrict__ smaps,
-                            const uint8_t *__restrict__ rowused, int j, int x, int nx, int r) {
-    const size_t n = (size_t)NY * nx;
-    const float2 *Tj = T + ((size_t)j * n + x) * r;
-    for (int e = threadIdx.x; e < NY * r; e += blockDim.x) {
-        const int y = e / r, l = e - y * r;
-        if (rowused[y]) cp_async8(tile + e, Tj + (size_t)y * nx * r + l);
-        else tile[e] = make_float2(0.f, 0.f);
-    }
-    for (int y = threadIdx.x; y < NY; y += blockDim.x) cp_async8(sS + y, smaps + (size_t)j * n + (size_t)y * nx + x);
-    cp_async_commit();
-}
+#define EACC 16    // tile elements per thread: NY r <= 256 * 16
 
 template <int P>
 __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
-                                                   const uint8_t *__restrict__ rowused, const float2 *__restrict__ Z,
-                                                   const float2 *__restrict__ B, float2 *__restrict__ Gout,
-                                                   float2 *__restrict__ gpart, unsigned int *counter,
-                                                   double *scal, int nx, int r, int q, int nc, int z_in_smem,
-                                                   double eta_c, const float2 *__restrict__ g_tw, float scale) {
+                                                   const uint8_t *__restrict__ rowused, float2 *__restrict__ Gk,
+                                                   int nx, int r, int nc, const float2 *__restrict__ g_tw,
+                                                   float scale) {
     constexpr int NY = 32 * P;
     extern __shared__ __align__(16) float2 smem[];
     float2 *tile0 = smem;                 // NY * r (two buffers)
@@ -220,35 +207,46 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
     float2 *sS0 = tile1 + NY * r;         // NY (two buffers)
     float2 *sS1 = sS0 + NY;
     float2 *s_tw = sS1 + NY;              // NY
-    float2 *sB = s_tw + NY;               // q * r
-    float2 *sZ = sB + q * r;              // NY * q when z_in_smem
-    __shared__ float s_c[16], s_s[16];
-    __shared__ float2 s_e[16];
-    __shared__ int s_cnt;
-    __shared__ float2 sA[RMAXC * RMAXC];
-    __shared__ double sP[RMAXC * (RMAXC + 1)];
     const int x = blockIdx.x;
-    if (z_in_smem) {
-        for (int e = threadIdx.x; e < NY * q; e += blockDim.x) {
-            const int y = e / q, k = e - y * q;
-            cp_async8(sZ + e, Z + ((size_t)y * nx + x) * q + k);
+    const size_t n = (size_t)NY * nx;
+    const int cnt = NY * r;
+    // this thread's tile elements e = tid + 256 u: global offset of (y, l) in a
+    // coil plane, or -1 for rows no frame samples
+    int goff[EACC];
+#pragma unroll
+    for (int u = 0; u < EACC; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        goff[u] = -2;
+        if (e < cnt) {
+            const int y = e / r, l = e - y * r;
+            goff[u] = rowused[y] ? (int)(((size_t)y * nx + x) * r + l) : -1;
         }
     }
-    cp_async_commit();
-    stage_column<NY>(tile0, sS0, T, smaps, rowused, 0, x, nx, r);
-    load_twiddles(s_tw, g_tw, NY);
-    for (int e = threadIdx.x; e < q * r; e += blockDim.x) sB[e] = B[e];
-    // each thread owns tile elements e = tid + 256 u (y = e / r, l = e % r) and
-    // accumulates conj(d_j) F_y^H(...) over the coils in registers
-    constexpr int ACC = (NY * RMAXC + 255) / 256;
-    float2 acc[ACC];
+    auto stage = [&](float2 *tile, float2 *sS, int j) {
+        const float2 *Tj = T + (size_t)j * n * r;
 #pragma unroll
-    for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
+        for (int u = 0; u < EACC; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            if (goff[u] >= 0) cp_async8(tile + e, Tj + goff[u]);
+            else if (goff[u] == -1) tile[e] = make_float2(0.f, 0.f);
+        }
+        for (int y = threadIdx.x; y < NY; y += blockDim.x) cp_async8(sS + y, smaps + (size_t)j * n + (size_t)y * nx + x);
+        cp_async_commit();
+    };
+    stage(tile0, sS0, 0);
+    load_twiddles(s_tw, g_tw, NY);
+    float2 acc[EACC];
+    int yy[EACC];
+#pragma unroll
+    for (int u = 0; u < EACC; ++u) {
+        acc[u] = make_float2(0.f, 0.f);
+        yy[u] = (threadIdx.x + 256 * u) / r;
+    }
     for (int j = 0; j < nc; ++j) {
         float2 *tile = (j & 1) ? tile1 : tile0;
         float2 *sS = (j & 1) ? sS1 : sS0;
         if (j + 1 < nc) {
-            stage_column<NY>((j & 1) ? tile0 : tile1, (j & 1) ? sS0 : sS1, T, smaps, rowused, j + 1, x, nx, r);
+            stage((j & 1) ? tile0 : tile1, (j & 1) ? sS0 : sS1, j + 1);
             cp_async_wait_1();
         } else {
             cp_async_wait();
@@ -256,73 +254,18 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
         __syncthreads();
         fft::tile_dft<NY, true>(tile, r, r, s_tw, scale);
 #pragma unroll
-        for (int u = 0; u < ACC; ++u) {
+        for (int u = 0; u < EACC; ++u) {
             const int e = threadIdx.x + 256 * u;
-            if (e < NY * r) cfmac(acc[u], sS[e / r], tile[e]);
+            if (e < cnt) cfmac(acc[u], sS[yy[u]], tile[e]);
         }
         __syncthreads();
     }
-    float2 *tile = tile0;
 #pragma unroll
-    for (int u = 0; u < ACC; ++u) {
+    for (int u = 0; u < EACC; ++u) {
         const int e = threadIdx.x + 256 * u;
-        if (e < NY * r) tile[e] = acc[u];
-    }
-    __syncthreads();
-    // grad = sum_j conj(d_j) F^H K_j - Z B^H, one thread per pixel of the column
-    for (int y = threadIdx.x; y < NY; y += blockDim.x) {
-        const size_t i = (size_t)y * nx + x;
-        float2 g[RMAXC];
-#pragma unroll
-        for (int l = 0; l < RMAXC; ++l) g[l] = (l < r) ? tile[y * r + l] : make_float2(0.f, 0.f);
-        const float2 *zr = z_in_smem ? sZ + (size_t)y * q : Z + i * q;
-        for (int k = 0; k < q; ++k) {
-            const float2 zk = zr[k];
-#pragma unroll
-            for (int l = 0; l < RMAXC; ++l)
-                if (l < r) {
-                    const float2 b = sB[k * r + l];
-                    // g -= zk * conj(b)
-                    g[l].x -= zk.x * b.x + zk.y * b.y;
-                    g[l].y -= zk.y * b.x - zk.x * b.y;
-                }
-        }
-#pragma unroll
-        for (int l = 0; l < RMAXC; ++l)
-            if (l < r) {
-                Gout[i * r + l] = g[l];
-                tile[y * r + l] = g[l];
-            }
-    }
-    __syncthreads();
-    const int np = r * (r + 1) / 2;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        int a, b;
-        pair_of(p, r, a, b);
-        float2 s = make_float2(0.f, 0.f);
-        for (int y = 0; y < NY; ++y) cfmac(s, tile[y * r + a], tile[y * r + b]);
-        gpart[(size_t)blockIdx.x * np + p] = s;
-    }
-    if (last_block_arrive(counter)) {
-        if (scal[SC_ETASET] == 0.0) {
-            // ||grad||_2 = sqrt(lambda_max(grad^H grad)); eta = eta_c / ||grad||_2 (Alg. 2, t = 1)
-            block_reduce_rows(gpart, gridDim.x, np, sP);
-            for (int p = threadIdx.x; p < np; p += blockDim.x) {
-                int a, b;
-                pair_of(p, r, a, b);
-                sA[a * r + b] = make_float2((float)sP[2 * p], (float)sP[2 * p + 1]);
-                sA[b * r + a] = make_float2((float)sP[2 * p], (float)-sP[2 * p + 1]);
-            }
-            __syncthreads();
-            block_jacobi(sA, r, r, nullptr, 0, s_c, s_s, s_e, &s_cnt, 30);
-            if (threadIdx.x == 0) {
-                float lmax = 0.f;
-                for (int a = 0; a < r; ++a) lmax = fmaxf(lmax, sA[a * r + a].x);
-                const double gn = sqrt((double)lmax);
-                scal[SC_GNORM] = gn;
-                scal[SC_ETA] = gn > 0.0 ? eta_c / gn : 0.0;
-                scal[SC_ETASET] = 1.0;
-            }
+        if (e < cnt) {
+            const int y = yy[u], l = e - y * r;
+            Gk[((size_t)y * nx + x) * r + l] = acc[u];
         }
     }
 }
@@ -334,11 +277,6 @@ static int fwd_tile_x(int r, int nx) {
     int tx = 2;
     while (tx * 2 * r <= 64 && tx * 2 <= nx) tx *= 2;
     return tx;
-}
-
-static size_t adj_cols_smem(const lrccs_ctx *c, int z_in_smem) {
-    const size_t ny = c->ny, r = c->r, q = c->q;
-    return (2 * ny * r + 2 * ny + ny + q * r + (z_in_smem ? ny * q : 0)) * sizeof(float2);
 }
 
 cudaError_t launch_iteration(lrccs_ctx *c) {
@@ -382,21 +320,21 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
             prof_end(c, KID_ADJ_ROWS);
         });
     }
-    // E
+    // E: coil-summed inverse transform into the U+ buffer (free during iterations)
     {
-        int z_in_smem = adj_cols_smem(c, 1) + 8192 <= (size_t)c->dev_smem_optin / 2;
-        const size_t smem = adj_cols_smem(c, z_in_smem);
+        const size_t smem = ((size_t)2 * ny * r + 3 * (size_t)ny) * sizeof(float2);
         DISPATCH_P(c->py, {
             prof_begin(c, KID_ADJ_COLS);
-            k_adj_cols<P_><<<nx, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowused, c->d_Z, c->d_B, c->d_G,
-                                                         c->d_gpart, c->d_counters + CNT_GRAD, c->d_scal, nx, r,
-                                                         c->q, c->nc, z_in_smem, c->prm.eta_c, c->d_twy, sy);
+            k_adj_cols<P_><<<nx, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowused, c->d_Up, nx, r, c->nc,
+                                                         c->d_twy, sy);
             prof_end(c, KID_ADJ_COLS);
         });
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // F, G, H
+    // F (gradient, Grams, eta, R1), G, H
+    e = launch_grad(c);
+    if (e != cudaSuccess) return e;
     return launch_qr(c, 1);
 }
 
