@@ -34,8 +34,7 @@ T_ITER = 50
 METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
 UNIT = "frame-iterations/s"
 FLUSH_BYTES = 256 << 20            # > 129 MB L2
-ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_grad",
-                "k_rinv_gram", "k_apply"]
+ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_gdqr"]
 
 
 def dist_env():
@@ -64,9 +63,7 @@ def kernel_bytes(name, p, r, n_used):
         "k_fwd_rows": 2 * C * r * nu,                    # read + write the sampled rows (in place)
         "k_adj_rows": 2 * C * r * nu,                    # read FU, write F_x^H(FU W)
         "k_adj_cols": C * r * nu + C * n + n * r,        # read rows, d_j; write sum_j conj(d_j) F^H K_j
-        "k_grad": 3 * n * r + n * q,                     # read that, U, Z; write grad
-        "k_rinv_gram": 2 * n * r,                        # read U, grad (U+ formed on the fly)
-        "k_apply": 4 * n * r + n * q,                    # read U, grad, Z; write U, U_{t-1}
+        "k_gdqr": 5 * n * r + n * q,                     # read that, U, Z; write grad, U_{t+1}, U_t
         "k_solve": 0,
     }.get(name, 0)
     return 8 * b
@@ -78,7 +75,7 @@ def iteration_bytes(p, r, n_used):
 
 def source_sha():
     h = hashlib.sha256()
-    for f in ("kernels_iter.cu", "kernels_small.cu", "common.cuh"):
+    for f in ("kernels_iter.cu", "kernels_solve.cu", "kernels_gd.cu", "common.cuh", "fft.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2212_09664_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

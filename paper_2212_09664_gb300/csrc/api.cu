@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <string>
 
 #include "internal.h"
@@ -24,7 +25,7 @@ void set_err(lrccs_ctx *c, const char *fmt, ...) {
 
 cudaError_t configure_kernels_init(int max_smem);
 cudaError_t configure_kernels_iter(int max_smem);
-cudaError_t configure_kernels_small(int max_smem);
+cudaError_t configure_kernels_gd(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -66,7 +67,7 @@ static void free_all(lrccs_ctx *c) {
     void *ptrs[] = {c->d_twy, c->d_twx, c->d_smaps, c->d_rowcnt, c->d_rowidx, c->d_framerows, c->d_lineptr,
                     c->d_rfptr, c->d_rflist, c->d_usedrows, c->d_rowused, c->d_idx, c->d_meta, c->d_status,
                     c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
-                    c->d_B, c->d_P, c->d_Hpart, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_R1inv, c->d_M};
+                    c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -123,7 +124,16 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     c->nblk = nblk;
     const int n = c->n, q = c->q, nc = c->nc, ny = c->ny;
     const int npm = rmax * (rmax + 1) / 2;
-    size_t gcap = (size_t)nblk * (2 * npm + rmax * rmax);   // k_grad's partial sums are the largest per block
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int gd = (c->n + 31) / 32;
+    if (gd > nsm) gd = nsm;
+    if (gd < 1) gd = 1;
+    c->gd_grid = gd;
+    const size_t gd_len = std::max((size_t)2 * npm + rmax * rmax, (size_t)rmax * rmax + (size_t)q * rmax);
+    size_t gcap = (size_t)gd * gd_len;
+    if ((size_t)nblk * rmax * rmax > gcap) gcap = (size_t)nblk * rmax * rmax;
     if ((size_t)c->nx * npm > gcap) gcap = (size_t)c->nx * npm;
     if ((size_t)152 * q * (q + 1) / 2 > gcap) gcap = (size_t)152 * q * (q + 1) / 2;
     if (gcap < 1024) gcap = 1024;
@@ -141,23 +151,23 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
               dalloc(c, &c->d_U, (size_t)n * rmax) && dalloc(c, &c->d_Uprev, (size_t)n * rmax) &&
               dalloc(c, &c->d_Up, (size_t)n * rmax) && dalloc(c, &c->d_G, (size_t)n * rmax) &&
               dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)c->ncg * ny * npm) &&
-              dalloc(c, &c->d_Hpart, (size_t)nblk * q * rmax) && dalloc(c, &c->d_gpart, gcap) &&
+              dalloc(c, &c->d_gpart, gcap) && dalloc(c, &c->d_tot, gd_len) &&
               dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)2 * q * q) &&
-              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_R1inv, (size_t)2 * rmax * rmax) &&
-              dalloc(c, &c->d_M, (size_t)rmax * rmax);
+              dalloc(c, &c->d_V, (size_t)q * q);
     if (!ok) {
         g_create_err = c->err;
         free_all(c);
         delete c;
         return LRCCS_E_NOMEM;
     }
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
+    int optin = 0, coop = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     c->dev_smem_optin = optin;
     cudaError_t e = configure_kernels_init(optin);
     if (e == cudaSuccess) e = configure_kernels_iter(optin);
-    if (e == cudaSuccess) e = configure_kernels_small(optin);
+    if (e == cudaSuccess) e = configure_kernels_gd(optin);
+    if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream);
@@ -230,6 +240,7 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     c->initialized = 0;
     c->t = 0;
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->d_meta, 0, MT_COUNT * sizeof(int32_t), c->stream));
     CK(cudaMemcpyAsync(c->d_smaps, d_smaps, (size_t)c->nc * c->n * sizeof(float2), cudaMemcpyDeviceToDevice,
@@ -268,7 +279,7 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
         return LRCCS_E_INVALID;
     }
     CK(launch_u0(c));
-    CK(launch_qr(c, 0));
+    CK(launch_gdqr(c, 0));
     CK(cudaMemcpyAsync(c->d_Uprev, c->d_U, (size_t)c->n * c->r * sizeof(float2), cudaMemcpyDeviceToDevice,
                        c->stream));
     s = sync_status(c);
@@ -377,8 +388,8 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
-    "k_eig", "k_u0", "k_gd_gram", "k_rinv_gram", "k_apply", "k_fwd_cols", "k_fwd_rows", "k_solve",
-    "k_adj_rows", "k_adj_cols", "k_images", "k_grad"};
+    "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols",
+    "k_images"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

@@ -311,6 +311,28 @@ LRCCS_DEV void fsum_add(fsum2 &acc, float x) {
     acc.hi = s;
     acc.lo += e;
 }
+// Warp-wide sum of (hi, lo) pairs, kept as a pair; identical in every lane.
+LRCCS_DEV fsum2 warp_fsum2(fsum2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o), ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        float s, e;
+        const bool first = (threadIdx.x & o) == 0;
+        two_sum(first ? v.hi : oh, first ? oh : v.hi, s, e);
+        v.lo = (first ? v.lo + ol : ol + v.lo) + e;
+        v.hi = s;
+    }
+    return v;
+}
+// (hi, lo) pair sum a + b (a first)
+LRCCS_DEV fsum2 fsum_pair(fsum2 a, fsum2 b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    fsum2 r;
+    r.hi = s;
+    r.lo = (a.lo + b.lo) + e;
+    return r;
+}
 // Warp-wide sum of (hi, lo) pairs; identical result in every lane.
 LRCCS_DEV double warp_fsum(fsum2 v) {
 #pragma unroll
@@ -406,6 +428,102 @@ LRCCS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "
 LRCCS_DEV void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // wait until at most one committed group is still pending (double buffering)
 LRCCS_DEV void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------- FP32 r x r factorisation
+
+// In place A = L L^H for a Hermitian r x r A (FP32, row-major, r <= RMAX) by
+// one warp, lane i holding row i in registers: the lower triangle of A
+// receives L, invd[i] = 1 / L[i][i].  Returns false (every lane) if a pivot
+// is not positive.
+template <int RMAX>
+LRCCS_DEV bool warp_chol32(float2 *A, int r, float *invd) {
+    const int i = threadIdx.x & 31;
+    float2 row[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) row[j] = (i < r && j <= i) ? A[i * r + j] : make_float2(0.f, 0.f);
+    float myinv = 1.f;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < RMAX; ++c) {
+        if (c < r && ok) {   // uniform across the warp
+            const float d = __shfl_sync(0xffffffffu, row[c].x, c);
+            ok = d > 0.f;
+            const float is = ok ? rsqrtf(d) : 0.f;
+            float2 lic = make_float2(0.f, 0.f);
+            if (i == c) {
+                lic = make_float2(d * is, 0.f);
+                myinv = is;
+            } else if (i > c && i < r) {
+                lic = cscale(row[c], is);
+            }
+            if (i >= c) row[c] = lic;
+#pragma unroll
+            for (int j = c + 1; j < RMAX; ++j) {
+                if (j < r) {
+                    const float ljx = __shfl_sync(0xffffffffu, lic.x, j), ljy = __shfl_sync(0xffffffffu, lic.y, j);
+                    if (i >= j && i < r) {   // A[i][j] -= L[i][c] conj(L[j][c])
+                        row[j].x -= lic.x * ljx + lic.y * ljy;
+                        row[j].y -= lic.y * ljx - lic.x * ljy;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    if (ok && i < r) {
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j)
+            if (j < r) A[i * r + j] = j <= i ? row[j] : make_float2(0.f, 0.f);
+        invd[i] = myinv;
+    }
+    __syncwarp();
+    return ok;
+}
+
+// Rinv = (L^H)^{-1} (upper triangular) for the factor L of warp_chol32 (r =
+// RMAX): lane j forms column j of L^{-1} in registers (forward substitution,
+// L read from shared memory) and stores row j of Rinv = its conjugate.
+template <int RMAX>
+LRCCS_DEV void warp_rinv32(const float2 *L, const float *invd, float2 *Rinv) {
+    const int j = threadIdx.x & 31;
+    float2 x[RMAX];
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) {
+        float2 s = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < i; ++m) {   // s -= L[i][m] x[m]  (x[m] = 0 for m < j)
+            const float2 l = L[i * RMAX + m];
+            s.x -= l.x * x[m].x - l.y * x[m].y;
+            s.y -= l.x * x[m].y + l.y * x[m].x;
+        }
+        x[i] = i >= j ? cscale(s, invd[i]) : make_float2(0.f, 0.f);
+    }
+    if (j < RMAX) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) Rinv[j * RMAX + i] = cconj(x[i]);
+    }
+    __syncwarp();
+}
+
+// Solve L L^H x = h (L from warp_chol32, lower triangle of the row-major r x r
+// FP32 matrix, invd = 1 / diag) by one warp; lane i holds h_i on entry and
+// returns x_i (lanes >= r return 0).  Right-looking substitutions.
+LRCCS_DEV float2 warp_chol_solve32(const float2 *L, const float *invd, int r, float2 h) {
+    const int i = threadIdx.x & 31;
+    for (int c = 0; c < r; ++c) {            // L z = h
+        const float2 hc = make_float2(__shfl_sync(0xffffffffu, h.x, c), __shfl_sync(0xffffffffu, h.y, c));
+        const float2 z = cscale(hc, invd[c]);
+        if (i == c) h = z;
+        else if (i > c && i < r) h = csub(h, cmul(L[i * r + c], z));
+    }
+    for (int c = r - 1; c >= 0; --c) {       // L^H x = z
+        const float2 hc = make_float2(__shfl_sync(0xffffffffu, h.x, c), __shfl_sync(0xffffffffu, h.y, c));
+        const float2 x = cscale(hc, invd[c]);
+        if (i == c) h = x;
+        else if (i < c) h = csub(h, cmulc(L[c * r + i], x));
+    }
+    return i < r ? h : make_float2(0.f, 0.f);
+}
 
 // ---------------------------------------------------------------- latency-lean FP64 r x r kernels
 // On this GPU a dependent FP64 FMA costs ~64 cycles and an FP64 square root or

@@ -31,13 +31,14 @@ enum {
 };
 
 // Grid-reduction counters.
-enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_GRAD, CNT_QR1, CNT_QR2, CNT_APPLY, CNT_COUNT = 8 };
+// CNT_BAR and CNT_BAR + 1: the grid-barrier and exit counters of k_gdqr.
+enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_COUNT = 8 };
 
 // Kernel ids (launch counting and optional CUDA-event timing).
 enum {
     KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
-    KID_EIG, KID_U0, KID_GD_GRAM, KID_RINV_GRAM, KID_APPLY, KID_FWD_COLS, KID_FWD_ROWS, KID_SOLVE,
-    KID_ADJ_ROWS, KID_ADJ_COLS, KID_IMAGES, KID_GRAD, KID_COUNT
+    KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_FWD_ROWS, KID_SOLVE, KID_ADJ_ROWS, KID_ADJ_COLS,
+    KID_IMAGES, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -64,7 +65,8 @@ struct lrccs_ctx {
     int t;             // iterations run since init
     int px, py;        // nx / 32, ny / 32
     int ncg;           // coil groups in the forward row pass
-    int nblk;          // blocks of the pixel-parallel kernels
+    int nblk;          // blocks of the pixel-parallel init kernels
+    int gd_grid;       // blocks of the cooperative GD/QR kernel (all resident)
     int n_used;        // host copy of MT_NUSED
     int n_lines;       // host copy of MT_NLINES
     int64_t total;     // fp[q] (samples per coil, all frames)
@@ -99,14 +101,12 @@ struct lrccs_ctx {
     float2 *d_G;                 // n * rmax  copy of the last gradient (diagnostics)
     float2 *d_B;                 // q * rmax
     float2 *d_P;                 // ncg * ny * npairs row Gram partials
-    float2 *d_Hpart;             // nblk * q * rmax
-    float2 *d_gpart;             // max(nblk, n_col_blocks, gram blocks) * max(npairs, q(q+1)/2)
+    float2 *d_gpart;             // partial sums of the grid reductions (init kernels, k_gdqr)
     size_t gpart_cap;
     double *d_sigma;             // q
     double *d_gram;              // 2 * q * q  X0^H X0 (FP64 re, im)
     float2 *d_V;                 // q * q eigenvectors of X0^H X0 (columns, sorted)
-    double *d_R1inv;             // r * r
-    float2 *d_M;                 // r * r  (R1 R2)^-1
+    double2 *d_tot;              // k_gdqr totals: [U_t^H U_{t+1} (r*r) | h = U^H Z (q*r)] after a launch
 };
 
 void set_err(lrccs_ctx *c, const char *fmt, ...);
@@ -121,8 +121,7 @@ cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);
 cudaError_t launch_u0(lrccs_ctx *c);
-cudaError_t launch_grad(lrccs_ctx *c);                 // F kernel (iteration)
-cudaError_t launch_qr(lrccs_ctx *c, int from_grad);   // F (init), G, H kernels
+cudaError_t launch_gdqr(lrccs_ctx *c, int mode);      // F: GD step + CholeskyQR2 (mode 0: init U+)
 cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);

@@ -1,0 +1,616 @@
+// kernels_gd.cu -- the GD step of Alg. 2 and its QR re-orthonormalisation as
+// one cooperative kernel (one block per SM, every block resident):
+//
+//   phase 1  grad = Gk - Z B^H  (Gk = sum_j conj(d_j) F^H K_j from the adjoint
+//            transforms), partial sums of grad^H grad, U^H grad, U^H U
+//   -------  grid reduction; every block: eta = eta_c / ||grad||_2 (t = 1),
+//            G1 = (U - eta grad)^H (U - eta grad)
+//                = U^H U - eta (U^H grad + grad^H U) + eta^2 grad^H grad,
+//            G1 = R1^H R1 (Cholesky), R1^{-1}
+//   phase 2  U_{t+1} = (U - eta grad) R1^{-1}  (the QR step of Alg. 2 as
+//            Cholesky QR), partial sums of U_t^H U_{t+1} (for SD) and
+//            U_{t+1}^H Z (the next B-step's right-hand sides h_k = U^H Z[:, k])
+//   -------  grid reduction; the last block out computes SD(U_t, U_{t+1}).
+//
+// G1 is formed from the exact U^H U of the current (FP32) iterate, so each
+// iteration removes the loss of orthogonality of the previous one; with
+// ||eta grad|| <= eta_c-sized steps G1 is well conditioned and one Cholesky
+// QR pass leaves U_{t+1} orthonormal to FP32 rounding.
+//
+// In init mode the same kernel orthonormalises the given U+ (G1 = U+^H U+).
+// A block's pixel range stays in shared memory across the phases when it
+// fits; otherwise each phase re-stages it in chunks.
+//
+// Partial sums are FP32 within a block and FP64 across blocks, reduced in a
+// fixed order (deterministic).  The grid barriers spin on a global counter
+// with an iteration limit: a barrier that gives up sets ST_TIMEOUT and the
+// kernel runs to completion with that status raised.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+#define RMAXC 16   // compile-time bound on the rank
+#define QMAXC 128  // compile-time bound on the number of frames
+#define NTG 512    // threads per block
+
+struct GdArgs {
+    const float2 *Gk;   // n x r   sum_j conj(d_j) F^H K_j (iteration mode)
+    const float2 *Z;    // n x q   A_k^H y_k, row-major (i q + k)
+    const float2 *B;    // q x r   B_t (row k = b_k)
+    float2 *U;          // n x r   U_t in, U_{t+1} out
+    float2 *Uprev;      // n x r   receives U_t (iteration mode)
+    const float2 *Up;   // n x r   U+ (init mode)
+    float2 *Gr;         // n x r   receives the gradient (iteration mode)
+    float2 *part;       // G x len partial sums
+    double2 *tot;       // len totals (FP64)
+    double *scal;       // SC_* scalars
+    unsigned int *bar;  // [0] barrier arrivals, [1] exit count
+    unsigned int *status;
+    int n, r, q, zs, chunk, resident, mode;
+    double eta_c;
+};
+
+// ---------------------------------------------------------------- grid-wide steps
+
+// Barrier number k (1, 2, ...) of this launch: wait until every block has
+// arrived k times.  Bounded: gives up after ~1 s and raises ST_TIMEOUT.
+static __device__ void grid_sync(unsigned int *bar, unsigned int k, unsigned int *status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = k * gridDim.x;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned int v = 0, spins = 0;
+        while (true) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (++spins > (1u << 24)) {
+                atomicOr(status, (unsigned)ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Block b reduces entries e = b, b + G, b + 2G, ... (< len) of the G partial
+// rows part[g len + e], four entries at a time (128 threads each), into FP64
+// totals: per thread in g order, then a fixed shuffle tree, then the warps in
+// order.
+static __device__ void grid_reduce(const float2 *part, int len, double2 *tot) {
+    __shared__ float4 s_w[NTG / 32];   // per warp: (re.hi, re.lo, im.hi, im.lo)
+    const int G = gridDim.x, l128 = threadIdx.x & 127, slot = threadIdx.x >> 7;
+    for (int j0 = 0; (int)blockIdx.x + G * j0 < len; j0 += NTG / 128) {
+        const int e = blockIdx.x + G * (j0 + slot);
+        fsum2 re = {0.f, 0.f}, im = {0.f, 0.f};
+        if (e < len)
+            for (int g = l128; g < G; g += 128) {
+                const float2 v = __ldcg(part + (size_t)g * len + e);
+                fsum_add(re, v.x);
+                fsum_add(im, v.y);
+            }
+        re = warp_fsum2(re);
+        im = warp_fsum2(im);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        __syncthreads();
+        if (l128 == 0 && e < len) {
+            float4 w = s_w[slot * 4];
+            fsum2 R = {w.x, w.y}, I = {w.z, w.w};
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                w = s_w[slot * 4 + k];
+                R = fsum_pair(R, fsum2{w.x, w.y});
+                I = fsum_pair(I, fsum2{w.z, w.w});
+            }
+            tot[e] = make_double2((double)R.hi + (double)R.lo, (double)I.hi + (double)I.lo);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- block helpers
+
+// Copy `rows` rows of `cols` complex values (global stride ss, shared stride
+// ds) with cp.async, 16 bytes per copy when everything is 16-byte aligned.
+static __device__ void stage_rows(float2 *dst, int ds, const float2 *src, int ss, int rows, int cols) {
+    if ((((uintptr_t)src | smem_u32(dst)) & 15) == 0 && ((ss | ds | cols) & 1) == 0) {
+        const int h = cols >> 1;
+        for (int e = threadIdx.x; e < rows * h; e += blockDim.x) {
+            const int i = e / h, c2 = e - i * h;
+            cp_async16(dst + i * ds + 2 * c2, src + (size_t)i * ss + 2 * c2);
+        }
+    } else {
+        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+            const int i = e / cols, c = e - i * cols;
+            cp_async8(dst + i * ds + c, src + (size_t)i * ss + c);
+        }
+    }
+}
+
+// G1 = L L^H and Rinv = (L^H)^{-1} by warp 0 (a separate function: it keeps
+// its own register allocation and schedule apart from the large kernel body).
+template <int R>
+static __device__ __noinline__ bool warp_chol_rinv(float2 *L, float *invd, float2 *Rinv) {
+    __syncwarp();   // run converged: the lanes may still be split after a single-lane branch
+    const bool ok = warp_chol32<R>(L, R, invd);
+    if (!ok) {
+        for (int e = threadIdx.x & 31; e < R * R; e += 32) L[e] = make_float2(e / R == e % R ? 1.f : 0.f, 0.f);
+        for (int e = threadIdx.x & 31; e < R; e += 32) invd[e] = 1.f;
+        __syncwarp();
+    }
+    warp_rinv32<R>(L, invd, Rinv);
+    return ok;
+}
+
+// 2 x 2 tile of a cross-Gram: acc[2 i + j] += sum_ii conj(X[ii][x_i]) Y[ii][y_j].
+struct Tile {
+    const float2 *X, *Y;
+    int xs, ys, x0, x1, y0, y1;
+};
+static __device__ void tile_accumulate(const Tile &g, float2 (&acc)[4], int s, int S, int cn) {
+    for (int ii = s; ii < cn; ii += S) {
+        const float2 p0 = g.X[ii * g.xs + g.x0], p1 = g.X[ii * g.xs + g.x1];
+        const float2 q0 = g.Y[ii * g.ys + g.y0], q1 = g.Y[ii * g.ys + g.y1];
+        cfmac(acc[0], p0, q0);
+        cfmac(acc[1], p0, q1);
+        cfmac(acc[2], p1, q0);
+        cfmac(acc[3], p1, q1);
+    }
+}
+
+// Combine the slices of up to two tile items per thread (item w = t + u NTG,
+// tile w mod T, slice w / T) and write entry m of tile w2 to
+// part[blockIdx.x * ld + out(w2, m)] (skipped when out < 0).  One round when
+// the scratch scr (cap complex values) holds all four entries of every item,
+// else one round per entry through s_red2 (2 NTG values).
+template <class OUT>
+static __device__ void tiles_write(const float2 (&acc)[2][4], int T, int S, float2 *scr, int cap, float2 *s_red2,
+                                   float2 *part, int ld, OUT out) {
+    const int W = S * T;
+    __syncthreads();
+    if (cap >= 4 * W) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int w = threadIdx.x + u * NTG;
+            if (w < W) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) scr[m * W + w] = acc[u][m];
+            }
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < 4 * T; it += NTG) {
+            const int m = it / T, w2 = it - m * T;
+            const int o = out(w2, m);
+            if (o >= 0) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int ss = 0; ss < S; ++ss) sum = cadd(sum, scr[m * W + ss * T + w2]);
+                part[(size_t)blockIdx.x * ld + o] = sum;
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int w = threadIdx.x + u * NTG;
+            if (w < W) s_red2[w] = acc[u][m];
+        }
+        __syncthreads();
+        for (int w2 = threadIdx.x; w2 < T; w2 += NTG) {
+            const int o = out(w2, m);
+            if (o >= 0) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int ss = 0; ss < S; ++ss) sum = cadd(sum, s_red2[ss * T + w2]);
+                part[(size_t)blockIdx.x * ld + o] = sum;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <int R>
+__global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
+    extern __shared__ __align__(16) float2 smem[];
+    constexpr int r = R;
+    const int q = a.q, zs = a.zs, chunk = a.chunk;
+    float2 *s_u = smem;                 // chunk * r : U_t (iteration) or U+ (init)
+    float2 *s_a = s_u + chunk * r;      // chunk * r : Gk, grad, then U_{t+1}
+    float2 *s_w = s_a + chunk * r;      // chunk * r : U - eta grad
+    float2 *s_z = s_w + chunk * r;      // chunk * zs: Z
+    __shared__ __align__(16) float2 sB[QMAXC * R];
+    __shared__ float2 sL[R * R];
+    __shared__ float2 sR[R * R];
+    __shared__ float sinv[R];
+    __shared__ float2 s_tot[2 * (R * (R + 1) / 2) + R * R];
+    __shared__ float2 s_red2[2 * NTG];
+    __shared__ float s_c[RMAXC], s_s[RMAXC];
+    __shared__ float2 s_e[RMAXC];
+    __shared__ int s_cnt, s_flag;
+    __shared__ float s_eta;
+    const int t = threadIdx.x, G = gridDim.x;
+    const int np = r * (r + 1) / 2, rr = r * r, tr = (r + 1) >> 1;
+    const int per = (a.n + G - 1) / G;
+    const int i0 = min(a.n, (int)blockIdx.x * per), i1 = min(a.n, i0 + per);
+    const bool iter = a.mode == 1;
+    // eta as it stands at launch; block 0 updates the device copy only after
+    // every block has passed the first barrier (so after every block read it)
+    const double eta_in = a.scal[SC_ETA];
+    const bool eta_set = a.scal[SC_ETASET] != 0.0;
+
+    // ------------------------------------------------ phase 1: gradient and Gram partial sums
+    // tiles: [grad^H grad (upper tiles) | U^H grad (all) | U^H U (upper tiles)], init: [U+^H U+]
+    const int th = tr * (tr + 1) / 2;
+    const int T1 = iter ? 2 * th + tr * tr : th;
+    const int len1 = iter ? 2 * np + rr : np;
+    const int S1 = max(1, NTG / T1);
+    auto tile1 = [&](int w, int &kind, int &A, int &Bt) {
+        if (!iter) {
+            kind = 2;
+            pair_of(w, tr, A, Bt);
+        } else if (w < th) {
+            kind = 0;
+            pair_of(w, tr, A, Bt);
+        } else if (w < th + tr * tr) {
+            kind = 1;
+            A = (w - th) / tr;
+            Bt = (w - th) - A * tr;
+        } else {
+            kind = 2;
+            pair_of(w - th - tr * tr, tr, A, Bt);
+        }
+    };
+    Tile g1[2];
+    int sl1[2];
+    float2 acc[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int w = t + u * NTG;
+        sl1[u] = w < S1 * T1 ? w / T1 : S1;   // S1 marks an idle item
+        int kind = 0, A = 0, Bt = 0;
+        if (w < S1 * T1) tile1(w % T1, kind, A, Bt);
+        g1[u].X = kind == 0 ? s_a : s_u;
+        g1[u].Y = kind == 2 ? s_u : s_a;
+        g1[u].xs = g1[u].ys = r;
+        g1[u].x0 = 2 * A;
+        g1[u].x1 = min(2 * A + 1, r - 1);
+        g1[u].y0 = 2 * Bt;
+        g1[u].y1 = min(2 * Bt + 1, r - 1);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[u][m] = make_float2(0.f, 0.f);
+    }
+    if (iter)
+        for (int e = t; e < q * r; e += NTG) cp_async8(sB + e, a.B + e);
+    for (int c0 = i0; c0 < i1; c0 += chunk) {
+        const int cn = min(chunk, i1 - c0);
+        __syncthreads();
+        if (iter) {
+            stage_rows(s_a, r, a.Gk + (size_t)c0 * r, r, cn, r);
+            stage_rows(s_u, r, a.U + (size_t)c0 * r, r, cn, r);
+        } else {
+            stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
+        }
+        stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
+        cp_async_commit();
+        cp_async_wait();
+        __syncthreads();
+        if (iter) {
+            // grad = Gk - Z B^H.  Thread = (pixel pair pp, part kq of the k range,
+            // NQ = NTG / 128 parts); the parts are subtracted from Gk in the fixed
+            // order NQ - 1, ..., 1, 0.
+            constexpr int NQ = NTG / 128;
+            const int pp = t & 127, kq = t >> 7;
+            const int K4 = ((q + 2 * NQ - 1) / (2 * NQ)) * 2;
+            const int k0 = min(q, kq * K4), k1 = min(q, k0 + K4);
+            const int p0 = min(2 * pp, cn - 1), p1 = min(2 * pp + 1, cn - 1);
+            float2 g0[R], g1v[R];
+#pragma unroll
+            for (int l = 0; l < R; ++l) g0[l] = g1v[l] = make_float2(0.f, 0.f);
+            const float2 *z0r = s_z + p0 * zs, *z1r = s_z + p1 * zs;
+            int k = k0;
+            for (; k + 1 < k1; k += 2) {
+                const float4 za = *(const float4 *)(z0r + k), zb = *(const float4 *)(z1r + k);
+#pragma unroll
+                for (int l = 0; l < R; ++l) {   // g += z_k conj(b_k[l]) + z_{k+1} conj(b_{k+1}[l])
+                    const float2 b0 = sB[k * r + l], b1 = sB[(k + 1) * r + l];
+                    g0[l].x = fmaf(za.x, b0.x, fmaf(za.y, b0.y, fmaf(za.z, b1.x, fmaf(za.w, b1.y, g0[l].x))));
+                    g0[l].y = fmaf(za.y, b0.x, fmaf(-za.x, b0.y, fmaf(za.w, b1.x, fmaf(-za.z, b1.y, g0[l].y))));
+                    g1v[l].x = fmaf(zb.x, b0.x, fmaf(zb.y, b0.y, fmaf(zb.z, b1.x, fmaf(zb.w, b1.y, g1v[l].x))));
+                    g1v[l].y = fmaf(zb.y, b0.x, fmaf(-zb.x, b0.y, fmaf(zb.w, b1.x, fmaf(-zb.z, b1.y, g1v[l].y))));
+                }
+            }
+            if (k < k1) {
+                const float2 za = z0r[k], zb = z1r[k];
+#pragma unroll
+                for (int l = 0; l < R; ++l) {
+                    const float2 b0 = sB[k * r + l];
+                    g0[l].x = fmaf(za.x, b0.x, fmaf(za.y, b0.y, g0[l].x));
+                    g0[l].y = fmaf(za.y, b0.x, fmaf(-za.x, b0.y, g0[l].y));
+                    g1v[l].x = fmaf(zb.x, b0.x, fmaf(zb.y, b0.y, g1v[l].x));
+                    g1v[l].y = fmaf(zb.y, b0.x, fmaf(-zb.x, b0.y, g1v[l].y));
+                }
+            }
+            const bool v0 = 2 * pp < cn, v1 = 2 * pp + 1 < cn;
+            for (int qq = NQ - 1; qq >= 0; --qq) {
+                if (kq == qq) {
+#pragma unroll
+                    for (int l = 0; l < R; ++l) {
+                        if (v0) s_a[p0 * r + l] = csub(s_a[p0 * r + l], g0[l]);
+                        if (v1) s_a[p1 * r + l] = csub(s_a[p1 * r + l], g1v[l]);
+                    }
+                }
+                __syncthreads();
+            }
+            for (int e = t; e < cn * r; e += NTG) a.Gr[(size_t)c0 * r + e] = s_a[e];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (sl1[u] < S1) tile_accumulate(g1[u], acc[u], sl1[u], S1, cn);
+    }
+    // partial row: [grad^H grad pairs (np) | U^H grad (rr) | U^H U pairs (np)], init: [U+^H U+ pairs]
+    tiles_write(acc, T1, S1, s_w, chunk * r, s_red2, a.part, len1, [&](int w, int m) {
+        int kind, A, Bt;
+        tile1(w, kind, A, Bt);
+        const int x = 2 * A + (m >> 1), y = 2 * Bt + (m & 1);
+        if (x >= r || y >= r) return -1;
+        if (kind == 1) return np + x * r + y;
+        if (x > y) return -1;
+        return (kind == 2 && iter ? np + rr : 0) + pair_index(x, y, r);
+    });
+    grid_sync(a.bar, 1, a.status);
+    grid_reduce(a.part, len1, a.tot);
+    grid_sync(a.bar, 2, a.status);
+    for (int e = t; e < len1; e += NTG) {
+        const double2 v = __ldcg(a.tot + e);
+        s_tot[e] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+
+    // ------------------------------------------------ G1 = R1^H R1 and R1^{-1} (every block)
+    if (iter) {
+        const float2 *A1 = s_tot, *A2 = s_tot + np, *A3 = s_tot + np + rr;
+        if (t == 0) s_eta = (float)eta_in;
+        if (!eta_set) {
+            // ||grad||_2^2 = lambda_max(grad^H grad) (Alg. 2, t = 1), FP32 Jacobi
+            for (int p = t; p < np; p += NTG) {
+                int x, y;
+                pair_of(p, r, x, y);
+                sR[x * r + y] = A1[p];
+                sR[y * r + x] = cconj(A1[p]);
+            }
+            __syncthreads();
+            block_jacobi(sR, r, r, nullptr, 0, s_c, s_s, s_e, &s_cnt, 30);
+            if (t == 0) {
+                float lmax = 0.f;
+                for (int x = 0; x < r; ++x) lmax = fmaxf(lmax, sR[x * r + x].x);
+                const double gn = sqrt((double)lmax);
+                const double eta = gn > 0.0 ? a.eta_c / gn : 0.0;
+                s_eta = (float)eta;
+                if (blockIdx.x == 0) {
+                    a.scal[SC_GNORM] = gn;
+                    a.scal[SC_ETA] = eta;
+                    a.scal[SC_ETASET] = 1.0;
+                }
+            }
+        }
+        __syncthreads();
+        const float eta = s_eta, eta2 = s_eta * s_eta;
+        for (int e = t; e < rr; e += NTG) {
+            const int x = e / r, y = e - x * r;
+            const int p = x <= y ? pair_index(x, y, r) : pair_index(y, x, r);
+            const float sg = x <= y ? 1.f : -1.f;   // lower half: conjugate of the stored pair
+            const float x2r = A2[x * r + y].x + A2[y * r + x].x;
+            const float x2i = A2[x * r + y].y - A2[y * r + x].y;
+            sL[e] = make_float2(A3[p].x - eta * x2r + eta2 * A1[p].x, sg * A3[p].y - eta * x2i + eta2 * sg * A1[p].y);
+        }
+    } else {
+        for (int e = t; e < rr; e += NTG) {
+            const int x = e / r, y = e - x * r;
+            const int p = x <= y ? pair_index(x, y, r) : pair_index(y, x, r);
+            sL[e] = x <= y ? s_tot[p] : cconj(s_tot[p]);
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        const bool ok = warp_chol_rinv<R>(sL, sinv, sR);
+        if (!ok && t == 0 && blockIdx.x == 0) atomicOr(a.status, (unsigned)ST_NOT_SPD_QR);
+    }
+    __syncthreads();
+    const float etaf = iter ? s_eta : 0.f;
+
+    // ------------------------------------------------ phase 2: U_{t+1} = (U - eta grad) R1^{-1}
+    // partial sums, all R columns per thread:
+    //   h-threads  t < Hth:           (k pair kp, slice s): conj(U_{t+1}[l]) Z[2kp + j]
+    //   C-threads  Hth <= t < Hth+Cth: (row x, slice s):    conj(U_t[x]) U_{t+1}[y]
+    const int tq = (q + 1) >> 1;
+    const int len2 = rr + q * r;
+    const int Sc = max(1, 64 / R), Cth = R * Sc;
+    const int Sh = max(1, (NTG - Cth) / tq), Hth = tq * Sh;
+    const bool hthr = t < Hth, cthr = !hthr && t < Hth + Cth;
+    const int hk = 2 * (t % tq), hs = t / tq;
+    const int cx = (t - Hth) % R, cs = (t - Hth) / R;
+    float2 pv[2 * R];
+#pragma unroll
+    for (int v = 0; v < 2 * R; ++v) pv[v] = make_float2(0.f, 0.f);
+    for (int c0 = i0; c0 < i1; c0 += chunk) {
+        const int cn = min(chunk, i1 - c0);
+        if (!a.resident) {
+            __syncthreads();
+            if (iter) {
+                stage_rows(s_u, r, a.U + (size_t)c0 * r, r, cn, r);
+                stage_rows(s_a, r, a.Gr + (size_t)c0 * r, r, cn, r);
+            } else {
+                stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
+            }
+            stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
+            cp_async_commit();
+            cp_async_wait();
+        }
+        __syncthreads();
+        for (int e = t; e < cn * r; e += NTG) s_w[e] = iter ? csub(s_u[e], cscale(s_a[e], etaf)) : s_u[e];
+        __syncthreads();
+        for (int e = t; e < cn * r; e += NTG) {
+            const int ii = e / r, l = e - ii * r;
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                if (m <= l) cfma(v, s_w[ii * r + m], sR[m * r + l]);
+            s_a[e] = v;
+        }
+        __syncthreads();
+        for (int e = t; e < cn * r; e += NTG) {
+            a.U[(size_t)c0 * r + e] = s_a[e];
+            if (iter) a.Uprev[(size_t)c0 * r + e] = s_u[e];
+        }
+        if (hthr) {
+            for (int ii = hs; ii < cn; ii += Sh) {
+                const float4 z = *(const float4 *)(s_z + ii * zs + hk);   // Z[k], Z[k+1] (pad column when k+1 = q)
+                const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
+#pragma unroll
+                for (int l = 0; l < R; ++l) {
+                    const float2 u = s_a[ii * r + l];
+                    cfmac(pv[l], u, z0);
+                    cfmac(pv[R + l], u, z1);
+                }
+            }
+        } else if (cthr) {
+            for (int ii = cs; ii < cn; ii += Sc) {
+                const float2 ux = s_u[ii * r + cx];
+#pragma unroll
+                for (int y = 0; y < R; ++y) cfmac(pv[y], ux, s_a[ii * r + y]);
+            }
+        }
+    }
+    // partial row: [U_t^H U_{t+1} (rr, x r + y) | h (q r, k r + l)]; slices summed in
+    // order, V values per thread per round (s_w and s_z are free after the last chunk)
+    {
+        const int cap2 = chunk * (r + zs);
+        float2 *scr = cap2 >= 2 * NTG ? s_w : s_red2;
+        const int V = max(2, min(2 * R, ((cap2 >= 2 * NTG ? cap2 : 2 * NTG) / NTG) & ~1));
+        for (int v0 = 0; v0 < 2 * R; v0 += V) {
+            __syncthreads();
+            if (hthr || cthr) {
+#pragma unroll
+                for (int v = 0; v < 2 * R; ++v)
+                    if (v >= v0 && v < v0 + V && (hthr || v < R)) scr[(v - v0) * NTG + t] = pv[v];
+            }
+            __syncthreads();
+            const int vn = min(V, 2 * R - v0);
+            for (int w = t; w < vn * (tq + R); w += NTG) {
+                const int dv = w / (tq + R), rem = w - dv * (tq + R), v = v0 + dv;
+                if (rem < tq) {
+                    const int kp = rem, k = 2 * kp + v / R, l = v % R;
+                    if (k < q) {
+                        float2 sum = make_float2(0.f, 0.f);
+                        for (int ss = 0; ss < Sh; ++ss) sum = cadd(sum, scr[dv * NTG + ss * tq + kp]);
+                        a.part[(size_t)blockIdx.x * len2 + rr + k * r + l] = sum;
+                    }
+                } else if (v < R) {
+                    const int x = rem - tq;
+                    float2 sum = make_float2(0.f, 0.f);
+                    for (int ss = 0; ss < Sc; ++ss) sum = cadd(sum, scr[dv * NTG + Hth + ss * R + x]);
+                    a.part[(size_t)blockIdx.x * len2 + x * r + v] = sum;
+                }
+            }
+        }
+    }
+    grid_sync(a.bar, 3, a.status);
+    grid_reduce(a.part, len2, a.tot);
+    // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2, and
+    // the barrier counters back to zero (every block is past its last barrier)
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.bar + 1, 1u);
+        s_flag = prev == (unsigned)G - 1;
+    }
+    __syncthreads();
+    if (!s_flag) return;
+    __threadfence();
+    if (t < 32) {
+        double sum = 0.0;
+        for (int e = t; e < rr; e += 32) {
+            const double2 v = __ldcg(a.tot + e);
+            sum += v.x * v.x + v.y * v.y;
+        }
+        sum = warp_sum_d(sum);
+        if (t == 0) {
+            if (iter) {
+                const double sd2 = (double)r - sum;
+                a.scal[SC_SD] = sqrt(sd2 > 0.0 ? sd2 : 0.0);
+            }
+            a.bar[0] = 0u;
+            a.bar[1] = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launcher
+
+typedef void (*gd_kernel_t)(GdArgs);
+static const gd_kernel_t kGd[RMAXC] = {k_gdqr<1>,  k_gdqr<2>,  k_gdqr<3>,  k_gdqr<4>,  k_gdqr<5>,  k_gdqr<6>,
+                                       k_gdqr<7>,  k_gdqr<8>,  k_gdqr<9>,  k_gdqr<10>, k_gdqr<11>, k_gdqr<12>,
+                                       k_gdqr<13>, k_gdqr<14>, k_gdqr<15>, k_gdqr<16>};
+static int g_gd_static_smem[RMAXC];
+
+cudaError_t configure_kernels_gd(int max_smem) {
+    for (int i = 0; i < RMAXC; ++i) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kGd[i]);
+        if (e != cudaSuccess) return e;
+        g_gd_static_smem[i] = (int)fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(kGd[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Z row stride in shared memory: q rounded up to 2 mod 4 complex values, so
+// that 16-byte loads of consecutive pixels' rows hit distinct banks.
+static int z_stride(int q) { return ((q + 1) | 3) - 1; }
+
+cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
+    const int r = c->r, q = c->q, G = c->gd_grid;
+    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
+    const int zs = z_stride(q);
+    const int per = (c->n + G - 1) / G;
+    const size_t bpp = (size_t)(3 * r + zs) * sizeof(float2);
+    const size_t avail = (size_t)(c->dev_smem_optin - g_gd_static_smem[r - 1]);
+    int chunk = (int)(avail / bpp) & ~1;
+    chunk = min(chunk, 256);
+    chunk = min(chunk, (per + 1) & ~1);
+    if (chunk < 2) return cudaErrorInvalidConfiguration;
+    GdArgs a;
+    a.Gk = c->d_Up;
+    a.Z = c->d_Z;
+    a.B = c->d_B;
+    a.U = c->d_U;
+    a.Uprev = c->d_Uprev;
+    a.Up = c->d_Up;
+    a.Gr = c->d_G;
+    a.part = c->d_gpart;
+    a.tot = c->d_tot;
+    a.scal = c->d_scal;
+    a.bar = c->d_counters + CNT_BAR;
+    a.status = c->d_status;
+    a.n = c->n;
+    a.r = r;
+    a.q = q;
+    a.zs = zs;
+    a.chunk = chunk;
+    a.resident = chunk >= per ? 1 : 0;
+    a.mode = mode;
+    a.eta_c = c->prm.eta_c;
+    void *args[] = {&a};
+    const size_t smem = (size_t)chunk * bpp;
+    prof_begin(c, KID_GDQR);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kGd[r - 1], dim3(G), dim3(NTG), args, smem, c->stream);
+    prof_end(c, KID_GDQR);
+    return e;
+}

@@ -11,14 +11,14 @@
 // With line masks W_i and the Gram contributions are constant along a sampled
 // row ky, so they are formed once per row.
 //
-// Kernels (one launch each per iteration; C and F-H are in kernels_small.cu):
+// Kernels (one launch each per iteration; C is in kernels_solve.cu, F in kernels_gd.cu):
 //   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l]
 //   B k_fwd_rows  : F_x of every sampled row of one coil, row Gram -> FU (in place), P[j][ky]
-//   C k_solve     : G_k = sum of its rows' P, h_k, FP64 Cholesky    -> B
+//   C k_solve     : G_k = sum of its rows' P, h_k, Cholesky         -> B
 //   D k_adj_rows  : K = FU W_ky, F_x^H                              -> T (in place)
 //   E k_adj_cols  : F_y^H, conj(d_j) coil sum                      -> Gk
-//   F k_grad      : grad = Gk - Z B^H, Grams, eta (t = 1), R1      (kernels_small.cu)
-//   G, H          : CholeskyQR2 of U - eta grad                    (kernels_small.cu)
+//   F k_gdqr      : grad = Gk - Z B^H, eta (t = 1), U - eta grad and its
+//                   CholeskyQR2, h = U^H Z, SD                      (kernels_gd.cu)
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
 #include <math.h>
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) k_adj_rows(float2 *__restrict__ T, const 
 
 // ---------------------------------------------------------------- E: adjoint, along y + coil sum
 // Gk = sum_j conj(d_j) o F_y^H (column x of coil j's row-transformed K_j);
-// the - Z B^H term and the Grams are added by k_grad (kernels_small.cu).
+// the - Z B^H term and the Grams are added by k_gdqr (kernels_gd.cu).
 
 #define EACC 16    // tile elements per thread: NY r <= 256 * 16
 
@@ -332,10 +332,8 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // F (gradient, Grams, eta, R1), G, H
-    e = launch_grad(c);
-    if (e != cudaSuccess) return e;
-    return launch_qr(c, 1);
+    // F: gradient, GD step and CholeskyQR2 (one cooperative launch)
+    return launch_gdqr(c, 1);
 }
 
 __global__ void k_images(const float2 *__restrict__ Uprev, const float2 *__restrict__ B, float2 *__restrict__ X,
