@@ -21,11 +21,14 @@
 //                   CholeskyQR2, h = U^H Z, SD                      (kernels_gd.cu)
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 #define DISPATCH_P(PV, ...)                                            \
     switch (PV) {                                                      \
@@ -192,10 +195,13 @@ __global__ void __launch_bounds__(256) k_adj_rows(float2 *__restrict__ T, const 
 // ---------------------------------------------------------------- E: adjoint, along y + coil sum
 // Gk = sum_j conj(d_j) o F_y^H (column x of coil j's row-transformed K_j);
 // the - Z B^H term and the Grams are added by k_gdqr (kernels_gd.cu).
+//
+// Grid (nx, CG) in thread-block clusters of (1, CG): block (x, g) handles
+// coils g, g + CG, g + 2 CG, ... of column x and keeps its partial sum in
+// registers; the CG partial tiles are then added through distributed shared
+// memory in rank order (deterministic), each block writing 1/CG of the column.
 
-#define EACC 16    // tile elements per thread: NY r <= 256 * 16
-
-template <int P>
+template <int P, int EA>   // EA: tile elements per thread, NY r <= 256 EA
 __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
                                                    const uint8_t *__restrict__ rowused, float2 *__restrict__ Gk,
                                                    int nx, int r, int nc, const float2 *__restrict__ g_tw,
@@ -207,14 +213,15 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
     float2 *sS0 = tile1 + NY * r;         // NY (two buffers)
     float2 *sS1 = sS0 + NY;
     float2 *s_tw = sS1 + NY;              // NY
-    const int x = blockIdx.x;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int x = blockIdx.x, g = blockIdx.y, CG = gridDim.y;
     const size_t n = (size_t)NY * nx;
     const int cnt = NY * r;
     // this thread's tile elements e = tid + 256 u: global offset of (y, l) in a
     // coil plane, or -1 for rows no frame samples
-    int goff[EACC];
+    int goff[EA];
 #pragma unroll
-    for (int u = 0; u < EACC; ++u) {
+    for (int u = 0; u < EA; ++u) {
         const int e = threadIdx.x + 256 * u;
         goff[u] = -2;
         if (e < cnt) {
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
     auto stage = [&](float2 *tile, float2 *sS, int j) {
         const float2 *Tj = T + (size_t)j * n * r;
 #pragma unroll
-        for (int u = 0; u < EACC; ++u) {
+        for (int u = 0; u < EA; ++u) {
             const int e = threadIdx.x + 256 * u;
             if (goff[u] >= 0) cp_async8(tile + e, Tj + goff[u]);
             else if (goff[u] == -1) tile[e] = make_float2(0.f, 0.f);
@@ -233,20 +240,17 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
         for (int y = threadIdx.x; y < NY; y += blockDim.x) cp_async8(sS + y, smaps + (size_t)j * n + (size_t)y * nx + x);
         cp_async_commit();
     };
-    stage(tile0, sS0, 0);
-    load_twiddles(s_tw, g_tw, NY);
-    float2 acc[EACC];
-    int yy[EACC];
+    float2 acc[EA];
 #pragma unroll
-    for (int u = 0; u < EACC; ++u) {
-        acc[u] = make_float2(0.f, 0.f);
-        yy[u] = (threadIdx.x + 256 * u) / r;
-    }
-    for (int j = 0; j < nc; ++j) {
-        float2 *tile = (j & 1) ? tile1 : tile0;
-        float2 *sS = (j & 1) ? sS1 : sS0;
-        if (j + 1 < nc) {
-            stage((j & 1) ? tile0 : tile1, (j & 1) ? sS0 : sS1, j + 1);
+    for (int u = 0; u < EA; ++u) acc[u] = make_float2(0.f, 0.f);
+    if (g < nc) stage(tile0, sS0, g);
+    load_twiddles(s_tw, g_tw, NY);
+    int b = 0;
+    for (int j = g; j < nc; j += CG, b ^= 1) {
+        float2 *tile = b ? tile1 : tile0;
+        float2 *sS = b ? sS1 : sS0;
+        if (j + CG < nc) {
+            stage(b ? tile0 : tile1, b ? sS0 : sS1, j + CG);
             cp_async_wait_1();
         } else {
             cp_async_wait();
@@ -254,23 +258,37 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
         __syncthreads();
         fft::tile_dft<NY, true>(tile, r, r, s_tw, scale);
 #pragma unroll
-        for (int u = 0; u < EACC; ++u) {
+        for (int u = 0; u < EA; ++u) {
             const int e = threadIdx.x + 256 * u;
-            if (e < cnt) cfmac(acc[u], sS[yy[u]], tile[e]);
+            if (e < cnt) cfmac(acc[u], sS[e / r], tile[e]);
         }
         __syncthreads();
     }
+    // partial tile of this block into its own tile0, then the cluster-wide sum
 #pragma unroll
-    for (int u = 0; u < EACC; ++u) {
+    for (int u = 0; u < EA; ++u) {
         const int e = threadIdx.x + 256 * u;
-        if (e < cnt) {
-            const int y = yy[u], l = e - y * r;
-            Gk[((size_t)y * nx + x) * r + l] = acc[u];
-        }
+        if (e < cnt) tile0[e] = acc[u];
     }
+    cluster.sync();
+    const int per = (cnt + CG - 1) / CG;
+    const int e0 = g * per, e1 = min(cnt, e0 + per);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int k = 0; k < CG; ++k) sum = cadd(sum, cluster.map_shared_rank(tile0, k)[e]);
+        const int y = e / r, l = e - y * r;
+        Gk[((size_t)y * nx + x) * r + l] = sum;
+    }
+    cluster.sync();   // no block leaves while its tile may still be read
 }
 
 // ---------------------------------------------------------------- launchers
+
+// Blocks per cluster of k_adj_cols: groups of about 4 coils, at most 8 blocks.
+static int adj_cluster(int nc) {
+    const int cg = (nc + 3) / 4;
+    return cg < 1 ? 1 : (cg > 8 ? 8 : cg);
+}
 
 // Columns per k_fwd_cols tile: even, and tx r <= 64 when possible.
 static int fwd_tile_x(int r, int nx) {
@@ -323,12 +341,32 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     // E: coil-summed inverse transform into the U+ buffer (free during iterations)
     {
         const size_t smem = ((size_t)2 * ny * r + 3 * (size_t)ny) * sizeof(float2);
+        const int cg = adj_cluster(c->nc);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nx, cg, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = cg;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const bool small = ny * r <= 256 * 8;
+        cudaError_t el = cudaSuccess;
         DISPATCH_P(c->py, {
             prof_begin(c, KID_ADJ_COLS);
-            k_adj_cols<P_><<<nx, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowused, c->d_Up, nx, r, c->nc,
-                                                         c->d_twy, sy);
+            if (small)
+                el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 8>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+                                        (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
+            else
+                el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 16>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+                                        (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
             prof_end(c, KID_ADJ_COLS);
         });
+        if (el != cudaSuccess) return el;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -354,7 +392,7 @@ cudaError_t launch_images(lrccs_ctx *c, float2 *d_X) {
     return cudaGetLastError();
 }
 
-#define SET_SMEM(fn) do { cudaError_t e_ = allow_smem(fn, max_smem); if (e_ != cudaSuccess) return e_; } while (0)
+#define SET_SMEM(...) do { cudaError_t e_ = allow_smem(__VA_ARGS__, max_smem); if (e_ != cudaSuccess) return e_; } while (0)
 #define SET_SMEM_P(fn) \
     SET_SMEM(fn<1>); SET_SMEM(fn<2>); SET_SMEM(fn<3>); SET_SMEM(fn<4>); \
     SET_SMEM(fn<5>); SET_SMEM(fn<6>); SET_SMEM(fn<7>); SET_SMEM(fn<8>)
@@ -362,6 +400,9 @@ cudaError_t configure_kernels_iter(int max_smem) {
     SET_SMEM_P(k_fwd_cols);
     SET_SMEM_P(k_fwd_rows);
     SET_SMEM_P(k_adj_rows);
-    SET_SMEM_P(k_adj_cols);
+    SET_SMEM(k_adj_cols<1, 8>); SET_SMEM(k_adj_cols<2, 8>); SET_SMEM(k_adj_cols<3, 8>); SET_SMEM(k_adj_cols<4, 8>);
+    SET_SMEM(k_adj_cols<5, 8>); SET_SMEM(k_adj_cols<6, 8>); SET_SMEM(k_adj_cols<7, 8>); SET_SMEM(k_adj_cols<8, 8>);
+    SET_SMEM(k_adj_cols<1, 16>); SET_SMEM(k_adj_cols<2, 16>); SET_SMEM(k_adj_cols<3, 16>); SET_SMEM(k_adj_cols<4, 16>);
+    SET_SMEM(k_adj_cols<5, 16>); SET_SMEM(k_adj_cols<6, 16>); SET_SMEM(k_adj_cols<7, 16>); SET_SMEM(k_adj_cols<8, 16>);
     return cudaSuccess;
 }
