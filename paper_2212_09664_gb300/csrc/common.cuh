@@ -90,6 +90,9 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
                              int *s_cnt, int max_sweeps, float abs_tol = 0.f) {
     const int n2 = n + (n & 1);
     const int npair = n2 / 2;
+    int sh = 0;                             // column index stride 2^sh >= n (no division per task)
+    while ((1 << sh) < n) ++sh;
+    const int mmask = (1 << sh) - 1;
     __shared__ short s_pp[64], s_qq[64];   // the pairs of the current round
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *s_cnt = 0;
@@ -105,15 +108,18 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
                 float2 e = make_float2(1.f, 0.f);
                 if (p < n && qq < n) {
                     const float2 apq = A[p * lda + qq];
-                    const float b = hypotf(apq.x, apq.y);
+                    const float b2 = apq.x * apq.x + apq.y * apq.y;
                     const float al = A[p * lda + p].x, ga = A[qq * lda + qq].x;
-                    if (b > 1e-30f && b > abs_tol && b > 1e-7f * sqrtf(fabsf(al) * fabsf(ga))) {
-                        e = make_float2(apq.x / b, apq.y / b);
-                        const float tau = (ga - al) / (2.f * b);
-                        const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                        c = rsqrtf(1.f + t * t);
+                    if (b2 > 1e-36f && b2 > abs_tol * abs_tol && b2 > 1e-14f * fabsf(al) * fabsf(ga)) {
+                        // the rotation only has to be orthogonal: c = 1 / sqrt(1 + t^2),
+                        // s = t c hold to rounding whatever the accuracy of t
+                        const float ib = rsqrtf(b2);
+                        e = make_float2(apq.x * ib, apq.y * ib);
+                        const float tau = (ga - al) * 0.5f * ib;
+                        const float t = copysignf(1.f, tau) * __frcp_rn(fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+                        c = rsqrtf(fmaf(t, t, 1.f));
                         s = t * c;
-                        atomicAdd(s_cnt, 1);
+                        *s_cnt = 1;
                     }
                 }
                 s_c[i] = c;
@@ -122,9 +128,9 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
             }
             __syncthreads();
             // rows p, q: A <- G^H A
-            for (int task = threadIdx.x; task < npair * n; task += blockDim.x) {
-                const int i = task / n, m = task - i * n;
-                if (s_s[i] == 0.f) continue;
+            for (int task = threadIdx.x; task < (npair << sh); task += blockDim.x) {
+                const int i = task >> sh, m = task & mmask;
+                if (m >= n || s_s[i] == 0.f) continue;
                 const int p = s_pp[i], qq = s_qq[i];
                 const float c = s_c[i], s = s_s[i];
                 const float2 e = s_e[i];
@@ -135,9 +141,9 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
             }
             __syncthreads();
             // columns p, q: A <- A G ; V <- V G
-            for (int task = threadIdx.x; task < npair * n; task += blockDim.x) {
-                const int i = task / n, m = task - i * n;
-                if (s_s[i] == 0.f) continue;
+            for (int task = threadIdx.x; task < (npair << sh); task += blockDim.x) {
+                const int i = task >> sh, m = task & mmask;
+                if (m >= n || s_s[i] == 0.f) continue;
                 const int p = s_pp[i], qq = s_qq[i];
                 const float c = s_c[i], s = s_s[i];
                 const float2 eh = cconj(s_e[i]);

@@ -100,7 +100,8 @@ struct lrccs_ctx {
     float2 *d_Up;                // n * rmax  gradient, then U+ = U - eta grad
     float2 *d_G;                 // n * rmax  copy of the last gradient (diagnostics)
     float2 *d_B;                 // q * rmax
-    float2 *d_P;                 // ncg * ny * npairs row Gram partials
+    float2 *d_P;                 // (ncg + 1) * ny * npairs row Grams: per coil, then coil-summed
+    unsigned int *d_rowarrive;   // ny  arrival counters of k_fwd_rows
     float2 *d_gpart;             // partial sums of the grid reductions (init kernels, k_gdqr)
     size_t gpart_cap;
     double *d_sigma;             // q

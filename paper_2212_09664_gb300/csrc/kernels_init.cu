@@ -393,9 +393,11 @@ __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int
     __syncthreads();
     fro = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fro += s_fro[w];
-    // off-diagonal entries below 1e-9 ||A||_F are under FP32 rounding of the
-    // largest entries; cyclic Jacobi converges quadratically, so 12 sweeps bound it
-    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 12, (float)(1e-9 * sqrt(fro)));
+    // rotations stop once every off-diagonal entry is below 1e-7 ||A||_F, i.e.
+    // at FP32 rounding of the largest entries (eigenvalues and vectors then
+    // carry relative errors ~1e-7); cyclic Jacobi converges quadratically, so
+    // 12 sweeps bound it
+    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 12, (float)(1e-7 * sqrt(fro)));
     if (v_in_smem)
         for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = Vw[(e / q) * ldv + e % q];
     // diagonal to a compact array (the sort below reads sA[i * q + i])
@@ -403,21 +405,19 @@ __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int
     if (threadIdx.x == 0)
         for (int i = 0; i < q; ++i) sA[i * q + i] = sA[i * ld + i];
     __syncthreads();
+    // eigenvalue order, descending (ties by index): thread i finds its rank
+    for (int i = threadIdx.x; i < q; i += blockDim.x) {
+        const float li = sA[i * q + i].x;
+        int rank = 0;
+        for (int j = 0; j < q; ++j) {
+            const float lj = sA[j * q + j].x;
+            rank += (lj > li || (lj == li && j < i)) ? 1 : 0;
+        }
+        order[rank] = i;
+        sigma[rank] = sqrt(li > 0.f ? (double)li : 0.0);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        // selection sort of the eigenvalue order, descending
-        for (int i = 0; i < q; ++i) order[i] = i;
-        for (int i = 0; i < q; ++i) {
-            int best = i;
-            for (int j = i + 1; j < q; ++j)
-                if (sA[order[j] * q + order[j]].x > sA[order[best] * q + order[best]].x) best = j;
-            int t = order[i];
-            order[i] = order[best];
-            order[best] = t;
-        }
-        for (int i = 0; i < q; ++i) {
-            double lam = (double)sA[order[i] * q + order[i]].x;
-            sigma[i] = sqrt(lam > 0.0 ? lam : 0.0);
-        }
         int r = rank_in;
         if (r <= 0) {
             long long capn = min(n, q);
@@ -457,7 +457,7 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     const int v_in_smem = (size_t)2 * q * ld * sizeof(float2) + 4096 <= (size_t)c->dev_smem_optin;
     const size_t smem2 = (size_t)(v_in_smem ? 2 : 1) * q * ld * sizeof(float2);
     prof_begin(c, KID_EIG);
-    k_eig<<<1, 1024, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
+    k_eig<<<1, 512, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
                                         c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem);
     prof_end(c, KID_EIG);
     return cudaGetLastError();

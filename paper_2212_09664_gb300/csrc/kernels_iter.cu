@@ -102,10 +102,12 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
 
 // ---------------------------------------------------------------- B: forward, along x + row Gram
 
+// The last of a row's nc blocks to finish also sums the row's coil partials
+// (in coil order) into Ppart[nc][ky], the coil-summed row Gram used by k_solve.
 template <int P>
 __global__ void __launch_bounds__(256) k_fwd_rows(float2 *__restrict__ T, const int32_t *__restrict__ usedrows,
-                                                   float2 *__restrict__ Ppart, int ny, int r,
-                                                   const float2 *__restrict__ g_tw, float scale) {
+                                                   float2 *__restrict__ Ppart, unsigned int *__restrict__ arrive,
+                                                   int ny, int r, const float2 *__restrict__ g_tw, float scale) {
     constexpr int NX = 32 * P;
     extern __shared__ __align__(16) float2 smem[];
     float2 *tile = smem;               // NX * r
@@ -137,6 +139,23 @@ __global__ void __launch_bounds__(256) k_fwd_rows(float2 *__restrict__ T, const 
         float2 s = make_float2(0.f, 0.f);
         for (int g = 0; g < KG; ++g) s = cadd(s, s_red[g * np + pp]);
         Ppart[((size_t)j * ny + ky) * np + pp] = s;
+    }
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(arrive + ky, 1u);
+        s_last = prev == gridDim.y - 1;
+        if (s_last) arrive[ky] = 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nc = gridDim.y;
+    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int g = 0; g < nc; ++g) s = cadd(s, __ldcg(Ppart + ((size_t)g * ny + ky) * np + pp));
+        Ppart[((size_t)nc * ny + ky) * np + pp] = s;
     }
 }
 
@@ -321,7 +340,8 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
         dim3 grid(c->n_used, c->nc);
         DISPATCH_P(c->px, {
             prof_begin(c, KID_FWD_ROWS);
-            k_fwd_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, ny, r, c->d_twx, sx);
+            k_fwd_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, c->d_rowarrive, ny, r,
+                                                           c->d_twx, sx);
             prof_end(c, KID_FWD_ROWS);
         });
     }
