@@ -113,9 +113,10 @@ lrccs_status lrccs_init(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_
                         const uint8_t *d_mask, const void *d_smaps, int32_t *out_rank);
 
 /* Run n_iter altGDmin iterations (Alg. 2, GDmin loop): B-step, gradient,
- * GD step, CholeskyQR2 re-orthonormalisation.  Asynchronous unless info is
- * non-NULL or exit_enabled is set (then it synchronises and reports the
- * device status).  After the call, X = U_{t-1} B_t is available through
+ * GD step, QR re-orthonormalisation (Cholesky QR of U - eta grad).
+ * Asynchronous unless info is non-NULL or exit_enabled is set (then it
+ * synchronises and reports the device status; a grid barrier that gave up
+ * reports LRCCS_E_TIMEOUT).  After the call, X = U_{t-1} B_t is available through
  * lrccs_get_factors / lrccs_get_images.  Errors: LRCCS_E_STATE (no init),
  * LRCCS_E_RANK_DEFICIENT, LRCCS_E_CUDA. */
 lrccs_status lrccs_iterate(lrccs_ctx *ctx, int32_t n_iter, lrccs_iter_info *info);

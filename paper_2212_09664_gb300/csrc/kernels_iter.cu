@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(256) k_fwd_rows(float2 *__restrict__ T, const 
         Ppart[((size_t)j * ny + ky) * np + pp] = s;
     }
     __shared__ bool s_last;
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {   // the fence after the barrier releases the whole block's writes
+        __threadfence();
         const unsigned int prev = atomicAdd(arrive + ky, 1u);
         s_last = prev == gridDim.y - 1;
         if (s_last) arrive[ky] = 0u;

@@ -203,7 +203,7 @@ def test_gradient_and_invariants():
     B1 = op.bstep(p.y, U0)
     Gr = op.grad(p.y, U0, B1)
     assert nrmse(G, Gr) < 1e-4
-    # LS optimality U^H grad = 0 and orthonormality after CholeskyQR2
+    # LS optimality U^H grad = 0 and orthonormality after the QR step
     assert np.linalg.norm(U0.conj().T @ G) / np.linalg.norm(G) < 1e-4
     U1 = s.subspace().cpu().numpy().astype(np.complex128)
     assert np.abs(U1.conj().T @ U1 - np.eye(p.rank)).max() < 1e-5
