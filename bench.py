@@ -34,7 +34,7 @@ T_ITER = 50
 METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
 UNIT = "frame-iterations/s"
 FLUSH_BYTES = 256 << 20            # > 129 MB L2
-ITER_KERNELS = ["k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols", "k_gdqr"]
+ITER_KERNELS = ["k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols", "k_gdqr"]
 
 
 def dist_env():
@@ -60,8 +60,8 @@ def kernel_bytes(name, p, r, n_used):
     nu = n_used * p.nx
     b = {
         "k_fwd_cols": n * r + C * n + C * r * nu,        # read U, d_j; write F_y(d_j o U) on sampled rows
-        "k_fwd_rows": 2 * C * r * nu,                    # read + write the sampled rows (in place)
-        "k_adj_rows": 2 * C * r * nu,                    # read FU, write F_x^H(FU W)
+        "k_row_gram": C * r * nu,                        # read the sampled rows
+        "k_row_w": 2 * C * r * nu,                       # read the sampled rows, write T W (in place)
         "k_adj_cols": C * r * nu + C * n + n * r,        # read rows, d_j; write sum_j conj(d_j) F^H K_j
         "k_gdqr": 5 * n * r + n * q,                     # read that, U, Z; write grad, U_{t+1}, U_t
         "k_solve": 0,

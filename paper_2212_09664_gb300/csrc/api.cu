@@ -67,7 +67,7 @@ static void free_all(lrccs_ctx *c) {
     void *ptrs[] = {c->d_twy, c->d_twx, c->d_smaps, c->d_rowcnt, c->d_rowidx, c->d_framerows, c->d_lineptr,
                     c->d_rfptr, c->d_rflist, c->d_usedrows, c->d_rowused, c->d_idx, c->d_meta, c->d_status,
                     c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
-                    c->d_B, c->d_P, c->d_rowarrive, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot};
+                    c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -118,7 +118,6 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     c->rmax = rmax;
     c->px = d.nx / 32;
     c->py = d.ny / 32;
-    c->ncg = d.ncoil;   // one coil per CTA in the forward row pass: row Grams are kept per coil
     int nblk = (c->n + 127) / 128;
     if (nblk > 152) nblk = 152;
     c->nblk = nblk;
@@ -150,8 +149,7 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
               dalloc(c, &c->d_X0, (size_t)n * q) && dalloc(c, &c->d_T, c->T_cap) &&
               dalloc(c, &c->d_U, (size_t)n * rmax) && dalloc(c, &c->d_Uprev, (size_t)n * rmax) &&
               dalloc(c, &c->d_Up, (size_t)n * rmax) && dalloc(c, &c->d_G, (size_t)n * rmax) &&
-              dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)(c->ncg + 1) * ny * npm) &&
-              dalloc(c, &c->d_rowarrive, (size_t)ny) &&
+              dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)ny * npm) &&
               dalloc(c, &c->d_gpart, gcap) && dalloc(c, &c->d_tot, gd_len) &&
               dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)2 * q * q) &&
               dalloc(c, &c->d_V, (size_t)q * q);
@@ -242,7 +240,6 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     c->t = 0;
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream));
-    CK(cudaMemsetAsync(c->d_rowarrive, 0, (size_t)c->ny * sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->d_meta, 0, MT_COUNT * sizeof(int32_t), c->stream));
     CK(cudaMemcpyAsync(c->d_smaps, d_smaps, (size_t)c->nc * c->n * sizeof(float2), cudaMemcpyDeviceToDevice,
@@ -390,7 +387,7 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
-    "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_fwd_rows", "k_solve", "k_adj_rows", "k_adj_cols",
+    "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {

@@ -37,7 +37,7 @@ enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_COUNT = 8 };
 // Kernel ids (launch counting and optional CUDA-event timing).
 enum {
     KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
-    KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_FWD_ROWS, KID_SOLVE, KID_ADJ_ROWS, KID_ADJ_COLS,
+    KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_ROW_GRAM, KID_SOLVE, KID_ROW_W, KID_ADJ_COLS,
     KID_IMAGES, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
@@ -64,7 +64,6 @@ struct lrccs_ctx {
     int initialized;   // lrccs_init succeeded
     int t;             // iterations run since init
     int px, py;        // nx / 32, ny / 32
-    int ncg;           // coil groups in the forward row pass
     int nblk;          // blocks of the pixel-parallel init kernels
     int gd_grid;       // blocks of the cooperative GD/QR kernel (all resident)
     int n_used;        // host copy of MT_NUSED
@@ -100,8 +99,7 @@ struct lrccs_ctx {
     float2 *d_Up;                // n * rmax  gradient, then U+ = U - eta grad
     float2 *d_G;                 // n * rmax  copy of the last gradient (diagnostics)
     float2 *d_B;                 // q * rmax
-    float2 *d_P;                 // (ncg + 1) * ny * npairs row Grams: per coil, then coil-summed
-    unsigned int *d_rowarrive;   // ny  arrival counters of k_fwd_rows
+    float2 *d_P;                 // ny * npairs coil-summed row Grams
     float2 *d_gpart;             // partial sums of the grid reductions (init kernels, k_gdqr)
     size_t gpart_cap;
     double *d_sigma;             // q

@@ -1,24 +1,26 @@
 // kernels_iter.cu -- the transform kernels of one altGDmin iteration (Alg. 2,
 // GDmin loop) on sm_103a.
 //
-// The iteration uses three exact rearrangements of Alg. 2 (linearity only):
-//   A_k U = H_k [F(d_j o U)]_j         -> C r forward 2D transforms per iteration,
-//                                          shared by every frame;
+// The iteration uses exact rearrangements of Alg. 2 (linearity only):
+//   A_k U = H_k [F(d_j o U)]_j         -> the transforms of U are shared by every frame;
 //   (A_k U)^H y_k = U^H Z[:, k]         -> the right-hand side never re-reads y;
 //   sum_k A_k^H (A_k U b_k - y_k) b_k^H
-//     = sum_j conj(d_j) o F^H [FU_j[i,:] W_i] - Z B^H,   W_i = sum_{k: i in Omega_k} b_k b_k^H
-//                                        -> C r inverse transforms per iteration.
-// With line masks W_i and the Gram contributions are constant along a sampled
-// row ky, so they are formed once per row.
+//     = sum_j conj(d_j) o F^H [FU_j[i,:] W_i] - Z B^H,   W_i = sum_{k: i in Omega_k} b_k b_k^H.
+// With masks that are unions of full k-space rows, H_k keeps whole rows and
+// W_i is constant along a row ky.  F = F_y F_x with a unitary F_x, and right
+// multiplication by W_ky (acting on the rank index) commutes with F_x, so
+//   F_x^H [F_x(T_j[ky, :]) W_ky] = T_j[ky, :] W_ky,   T_j = F_y(d_j o U),
+// and by Parseval the row Gram FU^H FU of a row equals T^H T of the same row:
+// one iteration needs only the C r column transforms F_y and F_y^H.
 //
 // Kernels (one launch each per iteration; C is in kernels_solve.cu, F in kernels_gd.cu):
-//   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l]
-//   B k_fwd_rows  : F_x of every sampled row of one coil, row Gram -> FU (in place), P[j][ky]
+//   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l] (sampled rows)
+//   B k_row_gram  : coil-summed row Gram sum_j T_j^H T_j per sampled row -> P[ky]
 //   C k_solve     : G_k = sum of its rows' P, h_k, Cholesky         -> B
-//   D k_adj_rows  : K = FU W_ky, F_x^H                              -> T (in place)
+//   D k_row_w     : T_j[ky, :] <- T_j[ky, :] W_ky                    -> T (in place)
 //   E k_adj_cols  : F_y^H, conj(d_j) coil sum                      -> Gk
 //   F k_gdqr      : grad = Gk - Z B^H, eta (t = 1), U - eta grad and its
-//                   CholeskyQR2, h = U^H Z, SD                      (kernels_gd.cu)
+//                   Cholesky QR, h = U^H Z, SD                      (kernels_gd.cu)
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
 #include <cooperative_groups.h>
@@ -100,115 +102,131 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
     }
 }
 
-// ---------------------------------------------------------------- B: forward, along x + row Gram
+// ---------------------------------------------------------------- B: row Gram
 
-// The last of a row's nc blocks to finish also sums the row's coil partials
-// (in coil order) into Ppart[nc][ky], the coil-summed row Gram used by k_solve.
-template <int P>
-__global__ void __launch_bounds__(256) k_fwd_rows(float2 *__restrict__ T, const int32_t *__restrict__ usedrows,
-                                                   float2 *__restrict__ Ppart, unsigned int *__restrict__ arrive,
-                                                   int ny, int r, const float2 *__restrict__ g_tw, float scale) {
-    constexpr int NX = 32 * P;
+// Block = sampled row ky; the row of every coil is staged in turn (double
+// buffered) and P[ky] = sum_j sum_x conj(T_j[ky][x][a]) T_j[ky][x][b] (a <= b)
+// accumulates in registers: thread = (2 x 2 tile of pairs, x slice).  The
+// slices are summed in order at the end (deterministic).
+template <int R>
+__global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, const int32_t *__restrict__ usedrows,
+                                                   float2 *__restrict__ Prow, int ny, int nx, int nc) {
+    constexpr int np = R * (R + 1) / 2, tr = (R + 1) / 2, nt = tr * (tr + 1) / 2;
+    constexpr int S = 256 / nt;            // x slices per tile
     extern __shared__ __align__(16) float2 smem[];
-    float2 *tile = smem;               // NX * r
-    float2 *s_tw = tile + NX * r;      // NX
-    float2 *s_red = s_tw + NX;         // KG * np
-    const int ky = usedrows[blockIdx.x], j = blockIdx.y;
-    const size_t n = (size_t)ny * NX;
-    float2 *row = T + ((size_t)j * n + (size_t)ky * NX) * r;
-    stage_row(tile, row, NX * r, threadIdx.x, blockDim.x);
+    float2 *tile0 = smem, *tile1 = smem + nx * R;
+    __shared__ float2 s_red[256 * 4];
+    const int ky = usedrows[blockIdx.x];
+    const size_t plane = (size_t)ny * nx * R;
+    const float2 *row0 = T + (size_t)ky * nx * R;
+    stage_row(tile0, row0, nx * R, threadIdx.x, blockDim.x);
     cp_async_commit();
-    load_twiddles(s_tw, g_tw, NX);
-    const int np = r * (r + 1) / 2;
-    const int KG = max(1, (int)blockDim.x / np);
-    const int p = threadIdx.x % np, kg = threadIdx.x / np;
-    const bool active = kg < KG;
-    int a = 0, b = 0;
-    pair_of(p, r, a, b);
-    cp_async_wait();
-    __syncthreads();
-    fft::tile_dft<NX, false>(tile, r, r, s_tw, scale);
-    for (int e = threadIdx.x; e < NX * r / 2; e += blockDim.x)
-        ((float4 *)row)[e] = ((const float4 *)tile)[e];
-    float2 acc = make_float2(0.f, 0.f);
-    if (active)
-        for (int kx = kg; kx < NX; kx += KG) cfmac(acc, tile[kx * r + a], tile[kx * r + b]);
-    if (active) s_red[kg * np + p] = acc;
-    __syncthreads();
-    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int g = 0; g < KG; ++g) s = cadd(s, s_red[g * np + pp]);
-        Ppart[((size_t)j * ny + ky) * np + pp] = s;
+    const int w = threadIdx.x % nt, sl = threadIdx.x / nt;
+    int A, Bt;
+    pair_of(w, tr, A, Bt);
+    const int x0 = 2 * A, x1 = min(2 * A + 1, R - 1), y0 = 2 * Bt, y1 = min(2 * Bt + 1, R - 1);
+    float2 acc[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
+    for (int j = 0; j < nc; ++j) {
+        const float2 *tile = (j & 1) ? tile1 : tile0;
+        if (j + 1 < nc) {
+            stage_row((j & 1) ? tile0 : tile1, row0 + (size_t)(j + 1) * plane, nx * R, threadIdx.x, blockDim.x);
+            cp_async_commit();
+            cp_async_wait_1();
+        } else {
+            cp_async_wait();
+        }
+        __syncthreads();
+        if (sl < S) {
+            for (int x = sl; x < nx; x += S) {
+                const float2 p0 = tile[x * R + x0], p1 = tile[x * R + x1];
+                const float2 q0 = tile[x * R + y0], q1 = tile[x * R + y1];
+                cfmac(acc[0], p0, q0);
+                cfmac(acc[1], p0, q1);
+                cfmac(acc[2], p1, q0);
+                cfmac(acc[3], p1, q1);
+            }
+        }
+        __syncthreads();
     }
-    __shared__ bool s_last;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s_red[m * 256 + threadIdx.x] = sl < S ? acc[m] : make_float2(0.f, 0.f);
     __syncthreads();
-    if (threadIdx.x == 0) {   // the fence after the barrier releases the whole block's writes
-        __threadfence();
-        const unsigned int prev = atomicAdd(arrive + ky, 1u);
-        s_last = prev == gridDim.y - 1;
-        if (s_last) arrive[ky] = 0u;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int nc = gridDim.y;
-    for (int pp = threadIdx.x; pp < np; pp += blockDim.x) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int g = 0; g < nc; ++g) s = cadd(s, __ldcg(Ppart + ((size_t)g * ny + ky) * np + pp));
-        Ppart[((size_t)nc * ny + ky) * np + pp] = s;
+    for (int it = threadIdx.x; it < 4 * nt; it += blockDim.x) {
+        const int m = it / nt, ww = it - m * nt;
+        int a2, b2;
+        pair_of(ww, tr, a2, b2);
+        const int a = 2 * a2 + (m >> 1), b = 2 * b2 + (m & 1);
+        if (a < R && b < R && a <= b) {
+            float2 sum = make_float2(0.f, 0.f);
+            for (int ss = 0; ss < S; ++ss) sum = cadd(sum, s_red[m * 256 + ss * nt + ww]);
+            Prow[(size_t)ky * np + pair_index(a, b, R)] = sum;
+        }
     }
 }
 
-// ---------------------------------------------------------------- D: adjoint, along x
+// ---------------------------------------------------------------- D: row times W
 
-template <int P>
-__global__ void __launch_bounds__(256) k_adj_rows(float2 *__restrict__ T, const float2 *__restrict__ B,
-                                                   const int32_t *__restrict__ usedrows,
-                                                   const int32_t *__restrict__ rfptr, const int32_t *__restrict__ rflist,
-                                                   int ny, int r, const float2 *__restrict__ g_tw, float scale) {
-    constexpr int NX = 32 * P;
+// Block = sampled row ky: W_ky = sum over the frames k sampling row ky of
+// b_k b_k^H (from B staged in shared memory), then for every coil in turn
+// (double buffered) T_j[ky][x][:] <- T_j[ky][x][:] W_ky in place.
+template <int R>
+__global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const float2 *__restrict__ B,
+                                                const int32_t *__restrict__ usedrows,
+                                                const int32_t *__restrict__ rfptr,
+                                                const int32_t *__restrict__ rflist, int ny, int nx, int nc, int q) {
     extern __shared__ __align__(16) float2 smem[];
-    float2 *tile = smem;                 // NX * r
-    float2 *s_tw = tile + NX * r;        // NX
-    float2 *sW = s_tw + NX;              // RMAXC * RMAXC
-    const int ky = usedrows[blockIdx.x], j = blockIdx.y;
-    const size_t n = (size_t)ny * NX;
-    float2 *row = T + ((size_t)j * n + (size_t)ky * NX) * r;
-    stage_row(tile, row, NX * r, threadIdx.x, blockDim.x);
+    float2 *tile0 = smem, *tile1 = smem + nx * R;
+    float2 *sB = tile1 + nx * R;           // q * R
+    __shared__ float2 sW[R * R];
+    __shared__ int s_f[256];
+    const int ky = usedrows[blockIdx.x];
+    const size_t plane = (size_t)ny * nx * R;
+    float2 *row0 = T + (size_t)ky * nx * R;
+    for (int e = threadIdx.x; e < q * R; e += blockDim.x) cp_async8(sB + e, B + e);
+    stage_row(tile0, row0, nx * R, threadIdx.x, blockDim.x);
     cp_async_commit();
-    load_twiddles(s_tw, g_tw, NX);
-    // W_ky = sum over the frames sampling row ky of b_k b_k^H (while the row arrives)
-    const int f0 = rfptr[ky], f1 = rfptr[ky + 1];
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        const int a = e / r, b = e - a * r;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int f = f0; f < f1; ++f) {
-            const int k = rflist[f];
-            cfma(acc, B[(size_t)k * r + a], cconj(B[(size_t)k * r + b]));
+    const int f0 = rfptr[ky], nf = rfptr[ky + 1] - f0;
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) s_f[f] = rflist[f0 + f];
+    constexpr int RH = (R + 1) / 2;
+    for (int j = 0; j < nc; ++j) {
+        const float2 *tile = (j & 1) ? tile1 : tile0;
+        if (j + 1 < nc) {
+            stage_row((j & 1) ? tile0 : tile1, row0 + (size_t)(j + 1) * plane, nx * R, threadIdx.x, blockDim.x);
+            cp_async_commit();
+            cp_async_wait_1();
+        } else {
+            cp_async_wait();
         }
-        sW[a * RMAXC + b] = acc;
-    }
-    cp_async_wait();
-    __syncthreads();
-    for (int kx = threadIdx.x; kx < NX; kx += blockDim.x) {
-        float2 f[RMAXC];
-#pragma unroll
-        for (int a = 0; a < RMAXC; ++a) f[a] = (a < r) ? tile[kx * r + a] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < RMAXC; ++b) {
-            if (b < r) {
+        __syncthreads();
+        if (j == 0) {
+            for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+                const int a = e / R, b = e - a * R;
                 float2 acc = make_float2(0.f, 0.f);
+                for (int f = 0; f < nf; ++f) cfma(acc, sB[s_f[f] * R + a], cconj(sB[s_f[f] * R + b]));
+                sW[e] = acc;
+            }
+            __syncthreads();
+        }
+        float2 *row = row0 + (size_t)j * plane;
+        for (int it = threadIdx.x; it < 2 * nx; it += blockDim.x) {   // thread = (x, half of the columns)
+            const int x = it >> 1, b0 = (it & 1) * RH;
+            float2 fv[R];
 #pragma unroll
-                for (int a = 0; a < RMAXC; ++a)
-                    if (a < r) cfma(acc, f[a], sW[a * RMAXC + b]);
-                tile[kx * r + b] = acc;
+            for (int a = 0; a < R; ++a) fv[a] = tile[x * R + a];
+#pragma unroll
+            for (int bb = 0; bb < RH; ++bb) {
+                if (b0 + bb < R) {
+                    float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int a = 0; a < R; ++a) cfma(o, fv[a], sW[a * R + b0 + bb]);
+                    row[x * R + b0 + bb] = o;
+                }
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    fft::tile_dft<NX, true>(tile, r, r, s_tw, scale);
-    for (int e = threadIdx.x; e < NX * r / 2; e += blockDim.x)
-        ((float4 *)row)[e] = ((const float4 *)tile)[e];
 }
 
 // ---------------------------------------------------------------- E: adjoint, along y + coil sum
@@ -316,11 +334,17 @@ static int fwd_tile_x(int r, int nx) {
     return tx;
 }
 
+typedef void (*row_gram_t)(const float2 *, const int32_t *, float2 *, int, int, int);
+typedef void (*row_w_t)(float2 *, const float2 *, const int32_t *, const int32_t *, const int32_t *, int, int, int,
+                        int);
+#define RANK_TABLE(K) {K<1>, K<2>, K<3>, K<4>, K<5>, K<6>, K<7>, K<8>, K<9>, K<10>, K<11>, K<12>, K<13>, K<14>, K<15>, K<16>}
+static const row_gram_t kRowGram[RMAXC] = RANK_TABLE(k_row_gram);
+static const row_w_t kRowW[RMAXC] = RANK_TABLE(k_row_w);
+
 cudaError_t launch_iteration(lrccs_ctx *c) {
     const int r = c->r, nx = c->nx, ny = c->ny;
-    const float sx = (float)(1.0 / sqrt((double)nx));
     const float sy = (float)(1.0 / sqrt((double)ny));
-    const int np = npairs_of(r);
+    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
     // A
     {
         const int tx = fwd_tile_x(r, nx);
@@ -335,28 +359,20 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     }
     // B
     {
-        const int KG = 256 / np > 0 ? 256 / np : 1;
-        const size_t smem = ((size_t)nx * r + nx + (size_t)KG * np) * sizeof(float2);
-        dim3 grid(c->n_used, c->nc);
-        DISPATCH_P(c->px, {
-            prof_begin(c, KID_FWD_ROWS);
-            k_fwd_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, c->d_rowarrive, ny, r,
-                                                           c->d_twx, sx);
-            prof_end(c, KID_FWD_ROWS);
-        });
+        const size_t smem = (size_t)2 * nx * r * sizeof(float2);
+        prof_begin(c, KID_ROW_GRAM);
+        kRowGram[r - 1]<<<c->n_used, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, ny, nx, c->nc);
+        prof_end(c, KID_ROW_GRAM);
     }
     // C
     launch_solve(c);
     // D
     {
-        const size_t smem = ((size_t)nx * r + nx + RMAXC * RMAXC) * sizeof(float2);
-        dim3 grid(c->n_used, c->nc);
-        DISPATCH_P(c->px, {
-            prof_begin(c, KID_ADJ_ROWS);
-            k_adj_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist,
-                                                           ny, r, c->d_twx, sx);
-            prof_end(c, KID_ADJ_ROWS);
-        });
+        const size_t smem = ((size_t)2 * nx * r + (size_t)c->q * r) * sizeof(float2);
+        prof_begin(c, KID_ROW_W);
+        kRowW[r - 1]<<<c->n_used, 256, smem, c->stream>>>(c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny,
+                                                          nx, c->nc, c->q);
+        prof_end(c, KID_ROW_W);
     }
     // E: coil-summed inverse transform into the U+ buffer (free during iterations)
     {
@@ -418,8 +434,10 @@ cudaError_t launch_images(lrccs_ctx *c, float2 *d_X) {
     SET_SMEM(fn<5>); SET_SMEM(fn<6>); SET_SMEM(fn<7>); SET_SMEM(fn<8>)
 cudaError_t configure_kernels_iter(int max_smem) {
     SET_SMEM_P(k_fwd_cols);
-    SET_SMEM_P(k_fwd_rows);
-    SET_SMEM_P(k_adj_rows);
+    for (int i = 0; i < RMAXC; ++i) {
+        SET_SMEM(kRowGram[i]);
+        SET_SMEM(kRowW[i]);
+    }
     SET_SMEM(k_adj_cols<1, 8>); SET_SMEM(k_adj_cols<2, 8>); SET_SMEM(k_adj_cols<3, 8>); SET_SMEM(k_adj_cols<4, 8>);
     SET_SMEM(k_adj_cols<5, 8>); SET_SMEM(k_adj_cols<6, 8>); SET_SMEM(k_adj_cols<7, 8>); SET_SMEM(k_adj_cols<8, 8>);
     SET_SMEM(k_adj_cols<1, 16>); SET_SMEM(k_adj_cols<2, 16>); SET_SMEM(k_adj_cols<3, 16>); SET_SMEM(k_adj_cols<4, 16>);

@@ -1,7 +1,7 @@
 // kernels_solve.cu -- the B-step of an altGDmin iteration (Alg. 2): for each
 // frame k the r x r least squares  G_k b_k = h_k  with
 //   G_k = (A_k U)^H (A_k U) = sum over the frame's sampled rows ky of the
-//         coil-summed row Grams P[nc][ky] (k_fwd_rows),
+//         coil-summed row Grams P[ky] (k_row_gram),
 //   h_k = (A_k U)^H y_k = U^H Z[:, k] (totals left by k_gdqr),
 // solved by an FP32 Cholesky factorisation, one block per frame.
 #include <math.h>
@@ -57,9 +57,8 @@ static const solve_kernel_t kSolve[RMAXC] = {k_solve<1>,  k_solve<2>,  k_solve<3
 
 cudaError_t launch_solve(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
-    const size_t np = (size_t)c->r * (c->r + 1) / 2;
     prof_begin(c, KID_SOLVE);
-    kSolve[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_P + (size_t)c->ncg * c->ny * np, c->d_tot, c->d_lineptr,
+    kSolve[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_P, c->d_tot, c->d_lineptr,
                                                  c->d_framerows, c->d_B, c->d_status);
     prof_end(c, KID_SOLVE);
     return cudaGetLastError();
