@@ -15,7 +15,7 @@
 //
 // Kernels (one launch each per iteration; C is in kernels_solve.cu, F in kernels_gd.cu):
 //   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l] (sampled rows)
-//   B k_row_gram  : coil-summed row Gram sum_j T_j^H T_j per sampled row -> P[ky]
+//   B k_row_gram  : coil-summed row Gram sum_j T_j^H T_j per sampled row -> P[ky] (clusters)
 //   C k_solve     : G_k = sum of its rows' P, h_k, Cholesky         -> B
 //   D k_row_w     : T_j[ky, :] <- T_j[ky, :] W_ky                    -> T (in place)
 //   E k_adj_cols  : F_y^H, conj(d_j) coil sum                      -> Gk
@@ -104,10 +104,11 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
 
 // ---------------------------------------------------------------- B: row Gram
 
-// Block = sampled row ky; the row of every coil is staged in turn (double
-// buffered) and P[ky] = sum_j sum_x conj(T_j[ky][x][a]) T_j[ky][x][b] (a <= b)
-// accumulates in registers: thread = (2 x 2 tile of pairs, x slice).  The
-// slices are summed in order at the end (deterministic).
+// Grid (sampled rows, CG) in clusters of (1, CG): block (ky, g) stages the
+// row of coils g, g + CG, ... in turn (double buffered) and accumulates
+// sum_j sum_x conj(T_j[ky][x][a]) T_j[ky][x][b] (a <= b) in registers: thread =
+// (2 x 2 tile of pairs, x slice).  The slices, then the CG blocks' partials
+// (through distributed shared memory), are summed in a fixed order into P[ky].
 template <int R>
 __global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, const int32_t *__restrict__ usedrows,
                                                    float2 *__restrict__ Prow, int ny, int nx, int nc) {
@@ -116,10 +117,12 @@ __global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, 
     extern __shared__ __align__(16) float2 smem[];
     float2 *tile0 = smem, *tile1 = smem + nx * R;
     __shared__ float2 s_red[256 * 4];
-    const int ky = usedrows[blockIdx.x];
+    __shared__ float2 s_part[np];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int ky = usedrows[blockIdx.x], g = blockIdx.y, CG = gridDim.y;
     const size_t plane = (size_t)ny * nx * R;
     const float2 *row0 = T + (size_t)ky * nx * R;
-    stage_row(tile0, row0, nx * R, threadIdx.x, blockDim.x);
+    if (g < nc) stage_row(tile0, row0 + (size_t)g * plane, nx * R, threadIdx.x, blockDim.x);
     cp_async_commit();
     const int w = threadIdx.x % nt, sl = threadIdx.x / nt;
     int A, Bt;
@@ -128,10 +131,11 @@ __global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, 
     float2 acc[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-    for (int j = 0; j < nc; ++j) {
-        const float2 *tile = (j & 1) ? tile1 : tile0;
-        if (j + 1 < nc) {
-            stage_row((j & 1) ? tile0 : tile1, row0 + (size_t)(j + 1) * plane, nx * R, threadIdx.x, blockDim.x);
+    int b = 0;
+    for (int j = g; j < nc; j += CG, b ^= 1) {
+        const float2 *tile = b ? tile1 : tile0;
+        if (j + CG < nc) {
+            stage_row(b ? tile0 : tile1, row0 + (size_t)(j + CG) * plane, nx * R, threadIdx.x, blockDim.x);
             cp_async_commit();
             cp_async_wait_1();
         } else {
@@ -157,20 +161,30 @@ __global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, 
         const int m = it / nt, ww = it - m * nt;
         int a2, b2;
         pair_of(ww, tr, a2, b2);
-        const int a = 2 * a2 + (m >> 1), b = 2 * b2 + (m & 1);
-        if (a < R && b < R && a <= b) {
+        const int a = 2 * a2 + (m >> 1), bq = 2 * b2 + (m & 1);
+        if (a < R && bq < R && a <= bq) {
             float2 sum = make_float2(0.f, 0.f);
             for (int ss = 0; ss < S; ++ss) sum = cadd(sum, s_red[m * 256 + ss * nt + ww]);
-            Prow[(size_t)ky * np + pair_index(a, b, R)] = sum;
+            s_part[pair_index(a, bq, R)] = sum;
         }
     }
+    cluster.sync();
+    if (g == 0) {
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            float2 sum = make_float2(0.f, 0.f);
+            for (int k = 0; k < CG; ++k) sum = cadd(sum, cluster.map_shared_rank(s_part, k)[p]);
+            Prow[(size_t)ky * np + p] = sum;
+        }
+    }
+    cluster.sync();   // no block leaves while its partial may still be read
 }
 
 // ---------------------------------------------------------------- D: row times W
 
-// Block = sampled row ky: W_ky = sum over the frames k sampling row ky of
-// b_k b_k^H (from B staged in shared memory), then for every coil in turn
-// (double buffered) T_j[ky][x][:] <- T_j[ky][x][:] W_ky in place.
+// Block (sampled row ky, coil group g): W_ky = sum over the frames k sampling
+// row ky of b_k b_k^H (from B staged in shared memory), then for coils g,
+// g + CG, ... in turn (double buffered) T_j[ky][x][:] <- T_j[ky][x][:] W_ky in
+// place.
 template <int R>
 __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const float2 *__restrict__ B,
                                                 const int32_t *__restrict__ usedrows,
@@ -181,26 +195,27 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
     float2 *sB = tile1 + nx * R;           // q * R
     __shared__ float2 sW[R * R];
     __shared__ int s_f[256];
-    const int ky = usedrows[blockIdx.x];
+    const int ky = usedrows[blockIdx.x], g = blockIdx.y, CG = gridDim.y;
     const size_t plane = (size_t)ny * nx * R;
     float2 *row0 = T + (size_t)ky * nx * R;
     for (int e = threadIdx.x; e < q * R; e += blockDim.x) cp_async8(sB + e, B + e);
-    stage_row(tile0, row0, nx * R, threadIdx.x, blockDim.x);
+    if (g < nc) stage_row(tile0, row0 + (size_t)g * plane, nx * R, threadIdx.x, blockDim.x);
     cp_async_commit();
     const int f0 = rfptr[ky], nf = rfptr[ky + 1] - f0;
     for (int f = threadIdx.x; f < nf; f += blockDim.x) s_f[f] = rflist[f0 + f];
     constexpr int RH = (R + 1) / 2;
-    for (int j = 0; j < nc; ++j) {
-        const float2 *tile = (j & 1) ? tile1 : tile0;
-        if (j + 1 < nc) {
-            stage_row((j & 1) ? tile0 : tile1, row0 + (size_t)(j + 1) * plane, nx * R, threadIdx.x, blockDim.x);
+    int b = 0;
+    for (int j = g; j < nc; j += CG, b ^= 1) {
+        const float2 *tile = b ? tile1 : tile0;
+        if (j + CG < nc) {
+            stage_row(b ? tile0 : tile1, row0 + (size_t)(j + CG) * plane, nx * R, threadIdx.x, blockDim.x);
             cp_async_commit();
             cp_async_wait_1();
         } else {
             cp_async_wait();
         }
         __syncthreads();
-        if (j == 0) {
+        if (j == g) {
             for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
                 const int a = e / R, b = e - a * R;
                 float2 acc = make_float2(0.f, 0.f);
@@ -321,17 +336,18 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
 
 // ---------------------------------------------------------------- launchers
 
-// Blocks per cluster of k_adj_cols: groups of about 4 coils, at most 8 blocks.
-static int adj_cluster(int nc) {
-    const int cg = (nc + 3) / 4;
-    return cg < 1 ? 1 : (cg > 8 ? 8 : cg);
-}
-
 // Columns per k_fwd_cols tile: even, and tx r <= 64 when possible.
 static int fwd_tile_x(int r, int nx) {
     int tx = 2;
     while (tx * 2 * r <= 64 && tx * 2 <= nx) tx *= 2;
     return tx;
+}
+
+// Coil groups (cluster size) of k_adj_cols, k_row_gram and k_row_w: groups of
+// about 4 coils, at most 8.
+static int adj_cluster(int nc) {
+    const int cg = (nc + 3) / 4;
+    return cg < 1 ? 1 : (cg > 8 ? 8 : cg);
 }
 
 typedef void (*row_gram_t)(const float2 *, const int32_t *, float2 *, int, int, int);
@@ -360,9 +376,24 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     // B
     {
         const size_t smem = (size_t)2 * nx * r * sizeof(float2);
+        const int cgr = adj_cluster(c->nc);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c->n_used, cgr, 1);
+        cfg.blockDim = dim3(256, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = cgr;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
         prof_begin(c, KID_ROW_GRAM);
-        kRowGram[r - 1]<<<c->n_used, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_P, ny, nx, c->nc);
+        const cudaError_t el = cudaLaunchKernelEx(&cfg, kRowGram[r - 1], (const float2 *)c->d_T,
+                                                  (const int32_t *)c->d_usedrows, c->d_P, ny, nx, c->nc);
         prof_end(c, KID_ROW_GRAM);
+        if (el != cudaSuccess) return el;
     }
     // C
     launch_solve(c);
@@ -370,8 +401,8 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     {
         const size_t smem = ((size_t)2 * nx * r + (size_t)c->q * r) * sizeof(float2);
         prof_begin(c, KID_ROW_W);
-        kRowW[r - 1]<<<c->n_used, 256, smem, c->stream>>>(c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny,
-                                                          nx, c->nc, c->q);
+        kRowW[r - 1]<<<dim3(c->n_used, adj_cluster(c->nc)), 256, smem, c->stream>>>(
+            c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny, nx, c->nc, c->q);
         prof_end(c, KID_ROW_W);
     }
     // E: coil-summed inverse transform into the U+ buffer (free during iterations)
