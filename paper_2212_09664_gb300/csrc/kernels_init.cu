@@ -313,7 +313,7 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
 #define MAXPP 17   // pairs per thread: q(q+1)/2 <= 512 * 17 for q <= 128
 
 __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restrict__ X0, int n, int q,
-                                                           float2 *part, unsigned int *counter, double *gram) {
+                                                           float2 *part) {
     extern __shared__ float2 s_x[];  // GRAM_CHUNK * q, then the pair table
     short2 *s_pair = (short2 *)(s_x + GRAM_CHUNK * q);
     const int np = q * (q + 1) / 2;
@@ -332,12 +332,15 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
         __syncthreads();
         for (int e = threadIdx.x; e < cn * q; e += blockDim.x) s_x[e] = X0[(size_t)c0 * q + e];
         __syncthreads();
+        for (int ii = 0; ii < cn; ++ii) {   // all of this thread's pairs per pixel (independent chains)
+            const float2 *xr = s_x + ii * q;
 #pragma unroll
-        for (int u = 0; u < MAXPP; ++u) {
-            const int p = threadIdx.x + GRAM_THREADS * u;
-            if (p < np) {
-                const short2 ab = s_pair[p];
-                for (int ii = 0; ii < cn; ++ii) cfmac(acc[u], s_x[ii * q + ab.x], s_x[ii * q + ab.y]);
+            for (int u = 0; u < MAXPP; ++u) {
+                const int p = threadIdx.x + GRAM_THREADS * u;
+                if (p < np) {
+                    const short2 ab = s_pair[p];
+                    cfmac(acc[u], xr[ab.x], xr[ab.y]);
+                }
             }
         }
     }
@@ -346,21 +349,52 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
         const int p = threadIdx.x + GRAM_THREADS * u;
         if (p < np) part[(size_t)blockIdx.x * np + p] = acc[u];
     }
-    if (last_block_arrive(counter)) {
-        for (int p = threadIdx.x; p < np; p += blockDim.x) {
-            double re = 0.0, im = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b) {
-                float2 v = __ldcg(part + (size_t)b * np + p);
-                re += v.x;
-                im += v.y;
+}
+
+// Sum the nblk partial rows of k_gram_x0 into the FP64 Hermitian Gram: thread
+// (pair p, slice s of 4) adds blocks s, s + 4, ... in compensated FP32 with 8
+// loads in flight; the 4 slices are then added in order.
+__global__ void __launch_bounds__(256) k_gram_sum(const float2 *__restrict__ part, int nblk, int q,
+                                                  double *__restrict__ gram) {
+    __shared__ float4 s_acc[256];
+    const int np = q * (q + 1) / 2;
+    const int pl = threadIdx.x & 63, sl = threadIdx.x >> 6;
+    const int p = blockIdx.x * 64 + pl;
+    fsum2 re = {0.f, 0.f}, im = {0.f, 0.f};
+    if (p < np) {
+        int b = sl;
+        for (; b + 28 < nblk; b += 32) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (size_t)(b + 4 * u) * np + p);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                fsum_add(re, v[u].x);
+                fsum_add(im, v[u].y);
             }
-            const short2 ab = s_pair[p];
-            const int a = ab.x, bb = ab.y;
-            gram[2 * (a * q + bb)] = re;
-            gram[2 * (a * q + bb) + 1] = im;
-            gram[2 * (bb * q + a)] = re;
-            gram[2 * (bb * q + a) + 1] = -im;
         }
+        for (; b < nblk; b += 4) {
+            const float2 v = __ldcg(part + (size_t)b * np + p);
+            fsum_add(re, v.x);
+            fsum_add(im, v.y);
+        }
+    }
+    s_acc[threadIdx.x] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    __syncthreads();
+    if (sl == 0 && p < np) {
+        fsum2 R = {s_acc[pl].x, s_acc[pl].y}, I = {s_acc[pl].z, s_acc[pl].w};
+        for (int k = 1; k < 4; ++k) {
+            const float4 w = s_acc[k * 64 + pl];
+            R = fsum_pair(R, fsum2{w.x, w.y});
+            I = fsum_pair(I, fsum2{w.z, w.w});
+        }
+        int a, bb;
+        pair_of(p, q, a, bb);
+        const double sr = (double)R.hi + (double)R.lo, si = (double)I.hi + (double)I.lo;
+        gram[2 * (a * q + bb)] = sr;
+        gram[2 * (a * q + bb) + 1] = si;
+        gram[2 * (bb * q + a)] = sr;
+        gram[2 * (bb * q + a) + 1] = -si;
     }
 }
 
@@ -448,8 +482,8 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     const size_t smem = (size_t)GRAM_CHUNK * q * sizeof(float2) + (size_t)np * sizeof(short2);
     double *gram = c->d_gram;
     prof_begin(c, KID_GRAM_X0);
-    k_gram_x0<<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart, c->d_counters + CNT_GRAMX0,
-                                                         gram);
+    k_gram_x0<<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    k_gram_sum<<<(np + 63) / 64, 256, 0, c->stream>>>(c->d_gpart, blocks, q, gram);
     prof_end(c, KID_GRAM_X0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -203,7 +203,9 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
     cp_async_commit();
     const int f0 = rfptr[ky], nf = rfptr[ky + 1] - f0;
     for (int f = threadIdx.x; f < nf; f += blockDim.x) s_f[f] = rflist[f0 + f];
-    constexpr int RH = (R + 1) / 2;
+    constexpr int NXG = 256 / R;           // x groups
+    const int wb = threadIdx.x % R, xg = threadIdx.x / R;
+    float2 wcol[R];
     int b = 0;
     for (int j = g; j < nc; j += CG, b ^= 1) {
         const float2 *tile = b ? tile1 : tile0;
@@ -223,21 +225,17 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
                 sW[e] = acc;
             }
             __syncthreads();
+#pragma unroll
+            for (int a = 0; a < R; ++a) wcol[a] = sW[a * R + wb];
         }
         float2 *row = row0 + (size_t)j * plane;
-        for (int it = threadIdx.x; it < 2 * nx; it += blockDim.x) {   // thread = (x, half of the columns)
-            const int x = it >> 1, b0 = (it & 1) * RH;
-            float2 fv[R];
+        if (xg < NXG) {   // thread = (output column wb, x group): W_ky[:, wb] in registers
+            for (int x = xg; x < nx; x += NXG) {
+                const float2 *fr = tile + x * R;
+                float2 o = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int a = 0; a < R; ++a) fv[a] = tile[x * R + a];
-#pragma unroll
-            for (int bb = 0; bb < RH; ++bb) {
-                if (b0 + bb < R) {
-                    float2 o = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int a = 0; a < R; ++a) cfma(o, fv[a], sW[a * R + b0 + bb]);
-                    row[x * R + b0 + bb] = o;
-                }
+                for (int a = 0; a < R; ++a) cfma(o, fr[a], wcol[a]);
+                row[x * R + wb] = o;
             }
         }
         __syncthreads();
