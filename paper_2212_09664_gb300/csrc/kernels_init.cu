@@ -312,6 +312,7 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
 #define GRAM_THREADS 512
 #define MAXPP 17   // pairs per thread: q(q+1)/2 <= 512 * 17 for q <= 128
 
+template <int NS>   // pair slots per thread: q(q+1)/2 <= GRAM_THREADS NS
 __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restrict__ X0, int n, int q,
                                                            float2 *part) {
     extern __shared__ float2 s_x[];  // GRAM_CHUNK * q, then the pair table
@@ -324,9 +325,9 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
     }
     const int per = (n + gridDim.x - 1) / gridDim.x;
     const int i0 = blockIdx.x * per, i1 = min(n, i0 + per);
-    float2 acc[MAXPP];
+    float2 acc[NS];
 #pragma unroll
-    for (int u = 0; u < MAXPP; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < NS; ++u) acc[u] = make_float2(0.f, 0.f);
     for (int c0 = i0; c0 < i1; c0 += GRAM_CHUNK) {
         const int cn = min(GRAM_CHUNK, i1 - c0);
         __syncthreads();
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
         for (int ii = 0; ii < cn; ++ii) {   // all of this thread's pairs per pixel (independent chains)
             const float2 *xr = s_x + ii * q;
 #pragma unroll
-            for (int u = 0; u < MAXPP; ++u) {
+            for (int u = 0; u < NS; ++u) {
                 const int p = threadIdx.x + GRAM_THREADS * u;
                 if (p < np) {
                     const short2 ab = s_pair[p];
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram_x0(const float2 *__restri
         }
     }
 #pragma unroll
-    for (int u = 0; u < MAXPP; ++u) {
+    for (int u = 0; u < NS; ++u) {
         const int p = threadIdx.x + GRAM_THREADS * u;
         if (p < np) part[(size_t)blockIdx.x * np + p] = acc[u];
     }
@@ -482,7 +483,14 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     const size_t smem = (size_t)GRAM_CHUNK * q * sizeof(float2) + (size_t)np * sizeof(short2);
     double *gram = c->d_gram;
     prof_begin(c, KID_GRAM_X0);
-    k_gram_x0<<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    const int ns = (np + GRAM_THREADS - 1) / GRAM_THREADS;
+    if (ns <= 1) k_gram_x0<1><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else if (ns <= 2) k_gram_x0<2><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else if (ns <= 3) k_gram_x0<3><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else if (ns <= 5) k_gram_x0<5><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else if (ns <= 8) k_gram_x0<8><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else if (ns <= 12) k_gram_x0<12><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
+    else k_gram_x0<MAXPP><<<blocks, GRAM_THREADS, smem, c->stream>>>(c->d_X0, c->n, q, c->d_gpart);
     k_gram_sum<<<(np + 63) / 64, 256, 0, c->stream>>>(c->d_gpart, blocks, q, gram);
     prof_end(c, KID_GRAM_X0);
     cudaError_t e = cudaGetLastError();
@@ -534,7 +542,8 @@ cudaError_t launch_u0(lrccs_ctx *c) {
 cudaError_t configure_kernels_init(int max_smem) {
     SET_SMEM(k_init_cols<1>); SET_SMEM(k_init_cols<2>); SET_SMEM(k_init_cols<3>); SET_SMEM(k_init_cols<4>);
     SET_SMEM(k_init_cols<5>); SET_SMEM(k_init_cols<6>); SET_SMEM(k_init_cols<7>); SET_SMEM(k_init_cols<8>);
-    SET_SMEM(k_gram_x0);
+    SET_SMEM(k_gram_x0<1>); SET_SMEM(k_gram_x0<2>); SET_SMEM(k_gram_x0<3>); SET_SMEM(k_gram_x0<5>);
+    SET_SMEM(k_gram_x0<8>); SET_SMEM(k_gram_x0<12>); SET_SMEM(k_gram_x0<MAXPP>);
     SET_SMEM(k_eig);
     SET_SMEM(k_u0);
     return cudaGetLastError();
