@@ -84,10 +84,10 @@ LRCCS_DEV bool last_block_arrive(unsigned int *counter) {
 // removes the phase of a_pq and applies the real 2x2 Jacobi rotation:
 // G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]], A <- G^H A G, V <- V G.
 // V (ldv columns, may be global memory) is updated when non-null.
-// A rotation is skipped when |a_pq| <= 1e-7 sqrt(|a_pp a_qq|) or |a_pq| <= abs_tol;
+// A rotation is skipped when |a_pq| <= rel_tol sqrt(|a_pp a_qq|) or |a_pq| <= abs_tol;
 // the sweeps stop when a whole sweep skips every rotation.
 __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ldv, float *s_c, float *s_s, float2 *s_e,
-                             int *s_cnt, int max_sweeps, float abs_tol = 0.f) {
+                             int *s_cnt, int max_sweeps, float abs_tol = 0.f, float rel_tol = 1e-7f) {
     const int n2 = n + (n & 1);
     const int npair = n2 / 2;
     int sh = 0;                             // column index stride 2^sh >= n (no division per task)
@@ -110,7 +110,7 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
                     const float2 apq = A[p * lda + qq];
                     const float b2 = apq.x * apq.x + apq.y * apq.y;
                     const float al = A[p * lda + p].x, ga = A[qq * lda + qq].x;
-                    if (b2 > 1e-36f && b2 > abs_tol * abs_tol && b2 > 1e-14f * fabsf(al) * fabsf(ga)) {
+                    if (b2 > 1e-36f && b2 > abs_tol * abs_tol && b2 > rel_tol * rel_tol * fabsf(al) * fabsf(ga)) {
                         // the rotation only has to be orthogonal: c = 1 / sqrt(1 + t^2),
                         // s = t c hold to rounding whatever the accuracy of t
                         const float ib = rsqrtf(b2);
