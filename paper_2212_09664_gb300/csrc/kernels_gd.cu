@@ -118,6 +118,12 @@ static __device__ void grid_reduce(const float2 *part, int len, double2 *tot) {
 static __device__ void stage_rows(float2 *dst, int ds, const float2 *src, int ss, int rows, int cols) {
     if ((((uintptr_t)src | smem_u32(dst)) & 15) == 0 && ((ss | ds | cols) & 1) == 0) {
         const int h = cols >> 1;
+        if (h <= (int)blockDim.x) {   // fixed (piece, row-step) mapping: no per-copy division
+            const int c2 = threadIdx.x % h, i0 = threadIdx.x / h, step = blockDim.x / h;
+            if (i0 < step)
+                for (int i = i0; i < rows; i += step) cp_async16(dst + i * ds + 2 * c2, src + (size_t)i * ss + 2 * c2);
+            return;
+        }
         for (int e = threadIdx.x; e < rows * h; e += blockDim.x) {
             const int i = e / h, c2 = e - i * h;
             cp_async16(dst + i * ds + 2 * c2, src + (size_t)i * ss + 2 * c2);

@@ -229,16 +229,28 @@ __global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0
     // thread owns tile elements e = tid + 256 u: yy = e / (2 TXI), cc = e % (2 TXI)
     constexpr int ACC = (NY * 2 * TXI + 255) / 256;
     float2 acc[ACC];
+    int goff[ACC];       // this thread's tile elements: offset in a coil's line block, or -1
 #pragma unroll
-    for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
-    for (int j = 0; j < nc; ++j) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < NY * 2 * TXI; e += blockDim.x) {
+    for (int u = 0; u < ACC; ++u) {
+        acc[u] = make_float2(0.f, 0.f);
+        const int e = threadIdx.x + 256 * u;
+        goff[u] = -1;
+        if (e < NY * 2 * TXI) {
             const int yy = e / (2 * TXI), cc = e % (2 * TXI);
             const int li = rowidx[k * NY + yy];
-            float2 v = make_float2(0.f, 0.f);
-            if (li >= 0) v = T0[(fbase + j * mk + (int64_t)li * nx + x0) * 2 + cc];
-            tile[yy * TP + cc] = v;
+            if (li >= 0) goff[u] = (li * nx + x0) * 2 + cc;
+        }
+    }
+    for (int j = 0; j < nc; ++j) {
+        __syncthreads();
+        const int64_t jb = (fbase + j * mk) * 2;
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            if (e < NY * 2 * TXI) {
+                const int yy = e / (2 * TXI), cc = e % (2 * TXI);
+                tile[yy * TP + cc] = goff[u] >= 0 ? T0[jb + goff[u]] : make_float2(0.f, 0.f);
+            }
         }
         for (int e = threadIdx.x; e < NY * TXI; e += blockDim.x)
             s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXI) * nx + x0 + (e % TXI)];

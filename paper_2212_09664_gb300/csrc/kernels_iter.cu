@@ -74,32 +74,36 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
     const int C = tx * r;
     const int x0 = blockIdx.x * tx, j = blockIdx.y;
     const size_t n = (size_t)NY * nx;
-    // one copy unit = (row y, 16-byte piece); rows of U are C complex, of d_j tx complex
+    // one copy unit = (row y, 16-byte piece); rows of U are C complex, of d_j tx
+    // complex.  Every loop uses a fixed (column, row-step) thread mapping, so no
+    // per-element division by the runtime row lengths.
     const int upr = C / 2, spr = tx / 2;
-    for (int e = threadIdx.x; e < NY * upr; e += blockDim.x) {
-        const int y = e / upr, c2 = e - y * upr;
-        cp_async16(tile + y * C + 2 * c2, U + ((size_t)y * nx + x0) * r + 2 * c2);
-    }
-    for (int e = threadIdx.x; e < NY * spr; e += blockDim.x) {
-        const int y = e / spr, c2 = e - y * spr;
-        cp_async16(sS + y * tx + 2 * c2, smaps + (size_t)j * n + (size_t)y * nx + x0 + 2 * c2);
+    const int uc = threadIdx.x % upr, uy = threadIdx.x / upr, ustep = blockDim.x / upr;
+    if (uy < ustep)
+        for (int y = uy; y < NY; y += ustep)
+            cp_async16(tile + y * C + 2 * uc, U + ((size_t)y * nx + x0) * r + 2 * uc);
+    {
+        const int sc = threadIdx.x % spr, sy = threadIdx.x / spr, sstep = blockDim.x / spr;
+        if (sy < sstep)
+            for (int y = sy; y < NY; y += sstep)
+                cp_async16(sS + y * tx + 2 * sc, smaps + (size_t)j * n + (size_t)y * nx + x0 + 2 * sc);
     }
     cp_async_commit();
     load_twiddles(s_tw, g_tw, NY);
     cp_async_wait();
     __syncthreads();
-    for (int e = threadIdx.x; e < NY * C; e += blockDim.x) {
-        const int y = e / C, c = e - y * C;
-        tile[e] = cmul(sS[y * tx + c / r], tile[e]);
+    {
+        const int mc = threadIdx.x % C, my = threadIdx.x / C, mstep = blockDim.x / C, mcol = mc / r;
+        if (my < mstep)
+            for (int y = my; y < NY; y += mstep) tile[y * C + mc] = cmul(sS[y * tx + mcol], tile[y * C + mc]);
     }
     __syncthreads();
     fft::tile_dft<NY, false>(tile, C, C, s_tw, scale);
     float2 *Tj = T + ((size_t)j * n + x0) * r;
-    for (int e = threadIdx.x; e < NY * upr; e += blockDim.x) {
-        const int ky = e / upr, c2 = e - ky * upr;
-        if (rowused[ky])
-            *(float4 *)(Tj + (size_t)ky * nx * r + 2 * c2) = *(const float4 *)(tile + ky * C + 2 * c2);
-    }
+    if (uy < ustep)
+        for (int ky = uy; ky < NY; ky += ustep)
+            if (rowused[ky])
+                *(float4 *)(Tj + (size_t)ky * nx * r + 2 * uc) = *(const float4 *)(tile + ky * C + 2 * uc);
 }
 
 // ---------------------------------------------------------------- B: row Gram
@@ -291,8 +295,12 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
         cp_async_commit();
     };
     float2 acc[EA];
+    int yy[EA];
 #pragma unroll
-    for (int u = 0; u < EA; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int u = 0; u < EA; ++u) {
+        acc[u] = make_float2(0.f, 0.f);
+        yy[u] = (threadIdx.x + 256 * u) / r;
+    }
     if (g < nc) stage(tile0, sS0, g);
     load_twiddles(s_tw, g_tw, NY);
     int b = 0;
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
 #pragma unroll
         for (int u = 0; u < EA; ++u) {
             const int e = threadIdx.x + 256 * u;
-            if (e < cnt) cfmac(acc[u], sS[e / r], tile[e]);
+            if (e < cnt) cfmac(acc[u], sS[yy[u]], tile[e]);
         }
         __syncthreads();
     }
