@@ -486,31 +486,6 @@ LRCCS_DEV bool warp_chol32(float2 *A, int r, float *invd) {
     return ok;
 }
 
-// Rinv = (L^H)^{-1} (upper triangular) for the factor L of warp_chol32 (r =
-// RMAX): lane j forms column j of L^{-1} in registers (forward substitution,
-// L read from shared memory) and stores row j of Rinv = its conjugate.
-template <int RMAX>
-LRCCS_DEV void warp_rinv32(const float2 *L, const float *invd, float2 *Rinv) {
-    const int j = threadIdx.x & 31;
-    float2 x[RMAX];
-#pragma unroll
-    for (int i = 0; i < RMAX; ++i) {
-        float2 s = make_float2(i == j ? 1.f : 0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < i; ++m) {   // s -= L[i][m] x[m]  (x[m] = 0 for m < j)
-            const float2 l = L[i * RMAX + m];
-            s.x -= l.x * x[m].x - l.y * x[m].y;
-            s.y -= l.x * x[m].y + l.y * x[m].x;
-        }
-        x[i] = i >= j ? cscale(s, invd[i]) : make_float2(0.f, 0.f);
-    }
-    if (j < RMAX) {
-#pragma unroll
-        for (int i = 0; i < RMAX; ++i) Rinv[j * RMAX + i] = cconj(x[i]);
-    }
-    __syncwarp();
-}
-
 // Solve L L^H x = h (L from warp_chol32, lower triangle of the row-major r x r
 // FP32 matrix, invd = 1 / diag) by one warp; lane i holds h_i on entry and
 // returns x_i (lanes >= r return 0).  Right-looking substitutions.
