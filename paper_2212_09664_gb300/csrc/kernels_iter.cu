@@ -255,45 +255,27 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
 // registers; the CG partial tiles are then added through distributed shared
 // memory in rank order (deterministic), each block writing 1/CG of the column.
 
-template <int P, int EA>   // EA: tile elements per thread, NY r <= 256 EA
+template <int P, int EA>   // EA: output tile elements per thread, NY r <= 256 EA
 __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
                                                    const uint8_t *__restrict__ rowused, float2 *__restrict__ Gk,
                                                    int nx, int r, int nc, const float2 *__restrict__ g_tw,
                                                    float scale) {
     constexpr int NY = 32 * P;
     extern __shared__ __align__(16) float2 smem[];
-    float2 *tile0 = smem;                 // NY * r (two buffers)
-    float2 *tile1 = tile0 + NY * r;
-    float2 *sS0 = tile1 + NY * r;         // NY (two buffers)
-    float2 *sS1 = sS0 + NY;
-    float2 *s_tw = sS1 + NY;              // NY
+    // two coils per transform call: tile[y][c r + l], c = 0, 1 (two buffers)
+    float2 *tile0 = smem;                 // NY * 2r
+    float2 *tile1 = tile0 + NY * 2 * r;
+    float2 *sS0 = tile1 + NY * 2 * r;     // 2 NY (two buffers)
+    float2 *sS1 = sS0 + 2 * NY;
+    float2 *s_tw = sS1 + 2 * NY;          // NY
     cg::cluster_group cluster = cg::this_cluster();
     const int x = blockIdx.x, g = blockIdx.y, CG = gridDim.y;
     const size_t n = (size_t)NY * nx;
-    const int cnt = NY * r;
-    // this thread's tile elements e = tid + 256 u: global offset of (y, l) in a
-    // coil plane, or -1 for rows no frame samples
-    int goff[EA];
-#pragma unroll
-    for (int u = 0; u < EA; ++u) {
-        const int e = threadIdx.x + 256 * u;
-        goff[u] = -2;
-        if (e < cnt) {
-            const int y = e / r, l = e - y * r;
-            goff[u] = rowused[y] ? (int)(((size_t)y * nx + x) * r + l) : -1;
-        }
-    }
-    auto stage = [&](float2 *tile, float2 *sS, int j) {
-        const float2 *Tj = T + (size_t)j * n * r;
-#pragma unroll
-        for (int u = 0; u < EA; ++u) {
-            const int e = threadIdx.x + 256 * u;
-            if (goff[u] >= 0) cp_async8(tile + e, Tj + goff[u]);
-            else if (goff[u] == -1) tile[e] = make_float2(0.f, 0.f);
-        }
-        for (int y = threadIdx.x; y < NY; y += blockDim.x) cp_async8(sS + y, smaps + (size_t)j * n + (size_t)y * nx + x);
-        cp_async_commit();
-    };
+    const int cnt = NY * r, r2 = 2 * r;
+    // this thread's output elements e = tid + 256 u hold (y, l) = (yy[u], e - yy[u] r);
+    // rows that no frame samples are zero-filled
+    __shared__ uint8_t s_used[32 * 8];
+    for (int y = threadIdx.x; y < NY; y += blockDim.x) s_used[y] = rowused[y];
     float2 acc[EA];
     int yy[EA];
 #pragma unroll
@@ -301,24 +283,55 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
         acc[u] = make_float2(0.f, 0.f);
         yy[u] = (threadIdx.x + 256 * u) / r;
     }
-    if (g < nc) stage(tile0, sS0, g);
+    __syncthreads();
+    // coils of this block: g, g + CG, g + 2 CG, ...; step s takes the pair (2s, 2s + 1) of them
+    const int mine = g < nc ? (nc - 1 - g) / CG + 1 : 0;
+    const int steps = (mine + 1) / 2;
+    auto stage = [&](float2 *tile, float2 *sS, int s) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int m = 2 * s + c;
+            const int j = g + m * CG;
+            const bool live = m < mine;
+            const float2 *Tj = T + (size_t)j * n * r + (size_t)x * r;
+#pragma unroll
+            for (int u = 0; u < EA; ++u) {
+                const int e = threadIdx.x + 256 * u;
+                if (e < cnt) {
+                    const int y = yy[u], l = e - y * r;
+                    float2 *dst = tile + y * r2 + c * r + l;
+                    if (live && s_used[y]) cp_async8(dst, Tj + (size_t)y * nx * r + l);
+                    else *dst = make_float2(0.f, 0.f);
+                }
+            }
+            for (int y = threadIdx.x; y < NY; y += blockDim.x) {
+                if (live) cp_async8(sS + c * NY + y, smaps + (size_t)j * n + (size_t)y * nx + x);
+                else sS[c * NY + y] = make_float2(0.f, 0.f);
+            }
+        }
+        cp_async_commit();
+    };
+    if (steps > 0) stage(tile0, sS0, 0);
     load_twiddles(s_tw, g_tw, NY);
-    int b = 0;
-    for (int j = g; j < nc; j += CG, b ^= 1) {
-        float2 *tile = b ? tile1 : tile0;
-        float2 *sS = b ? sS1 : sS0;
-        if (j + CG < nc) {
-            stage(b ? tile0 : tile1, b ? sS0 : sS1, j + CG);
+    for (int s = 0; s < steps; ++s) {
+        float2 *tile = (s & 1) ? tile1 : tile0;
+        float2 *sS = (s & 1) ? sS1 : sS0;
+        if (s + 1 < steps) {
+            stage((s & 1) ? tile0 : tile1, (s & 1) ? sS0 : sS1, s + 1);
             cp_async_wait_1();
         } else {
             cp_async_wait();
         }
         __syncthreads();
-        fft::tile_dft<NY, true>(tile, r, r, s_tw, scale);
+        fft::tile_dft<NY, true>(tile, r2, r2, s_tw, scale);
 #pragma unroll
         for (int u = 0; u < EA; ++u) {
             const int e = threadIdx.x + 256 * u;
-            if (e < cnt) cfmac(acc[u], sS[yy[u]], tile[e]);
+            if (e < cnt) {
+                const int y = yy[u], l = e - y * r;
+                cfmac(acc[u], sS[y], tile[y * r2 + l]);
+                cfmac(acc[u], sS[NY + y], tile[y * r2 + r + l]);
+            }
         }
         __syncthreads();
     }
@@ -413,7 +426,7 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     }
     // E: coil-summed inverse transform into the U+ buffer (free during iterations)
     {
-        const size_t smem = ((size_t)2 * ny * r + 3 * (size_t)ny) * sizeof(float2);
+        const size_t smem = ((size_t)4 * ny * r + 5 * (size_t)ny) * sizeof(float2);
         const int cg = adj_cluster(c->nc);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nx, cg, 1);
