@@ -116,9 +116,15 @@ lrccs_status lrccs_init(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_
  * GD step, QR re-orthonormalisation (Cholesky QR of U - eta grad).
  * Asynchronous unless info is non-NULL or exit_enabled is set (then it
  * synchronises and reports the device status; a grid barrier that gave up
- * reports LRCCS_E_TIMEOUT).  After the call, X = U_{t-1} B_t is available through
- * lrccs_get_factors / lrccs_get_images.  Errors: LRCCS_E_STATE (no init),
- * LRCCS_E_RANK_DEFICIENT, LRCCS_E_CUDA. */
+ * reports LRCCS_E_TIMEOUT).  Without exit_enabled and for n_iter > 1 the
+ * n_iter iterations run as one CUDA graph captured on the context's stream
+ * the first time a given n_iter (and set of timed kernels) is used and
+ * replayed afterwards; the context's stream must then be a created stream
+ * (on the legacy default stream, or while the caller is itself capturing
+ * that stream, the kernels are launched one by one instead).  After the
+ * call, X = U_{t-1} B_t is available through lrccs_get_factors /
+ * lrccs_get_images.  Errors: LRCCS_E_STATE (no init), LRCCS_E_RANK_DEFICIENT,
+ * LRCCS_E_CUDA. */
 lrccs_status lrccs_iterate(lrccs_ctx *ctx, int32_t n_iter, lrccs_iter_info *info);
 
 /* Copy the output pair of the last iteration: d_U <- U_{t-1} (n x r), d_B <- B_t
@@ -152,7 +158,10 @@ lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, s
  * kernels whose name contains `pattern` ("*" = all; NULL or "" = none).
  * lrccs_profile_read synchronises the stream, folds the pending events into the
  * totals and fills up to `max` entries of `out` (one per kernel, in a fixed
- * order); *count receives the number of kernels.  Names are static strings. */
+ * order); *count receives the number of kernels.  Names are static strings.
+ * Inside a replayed iteration graph (lrccs_iterate) the event records are graph
+ * nodes placed on every 8th iteration (the `timed` count says how many), and
+ * every replay since the last read reports the timings of the latest replay. */
 typedef struct lrccs_kernel_stat {
     const char *name;     /* kernel name */
     int64_t launches;     /* launches since the last reset */

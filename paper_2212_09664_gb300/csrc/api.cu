@@ -182,14 +182,20 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     return LRCCS_OK;
 }
 
+static void drop_iter_graph(lrccs_ctx *c);
+
 extern "C" void lrccs_destroy(lrccs_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     for (const prof_rec &r : c->pending) {
+        if (r.graph_owned) continue;   // owned by the graph, released below
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    c->pending.clear();
+    drop_iter_graph(c);                // its events go back to the pool
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    c->event_pool.clear();
     free_all(c);
     delete c;
 }
@@ -288,6 +294,96 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     return LRCCS_OK;
 }
 
+// Capture n iterations (launch_iteration's kernels and, when kernels are being
+// timed, their event records; nothing else) as one CUDA graph on the
+// context's stream, cached per (n, timed kernels, rank, sampled rows, work
+// buffer).  Returns false when the graph cannot be built here (the legacy
+// default stream cannot be captured); the caller then launches directly.
+static void drop_iter_graph(lrccs_ctx *c) {
+    if (!c->iter_exec) return;
+    cudaStreamSynchronize(c->stream);
+    cudaGraphExecDestroy(c->iter_exec);
+    c->iter_exec = nullptr;
+    for (const prof_rec &r : c->iter_prof) {
+        c->event_pool.push_back(r.a);
+        c->event_pool.push_back(r.b);
+    }
+    c->iter_prof.clear();
+}
+
+static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
+    if (c->iter_graph_failed) return false;
+    if (c->iter_exec && c->iter_n == n_iter && c->iter_mask == c->prof_mask && c->iter_r == c->r &&
+        c->iter_nused == c->n_used && c->iter_T == c->d_T)
+        return true;
+    if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread) {
+        c->iter_graph_failed = true;
+        return false;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;   // the caller is capturing this stream: launch into its capture
+    }
+    drop_iter_graph(c);
+    if (c->prof_mask) {   // timing events are created now, not during the capture
+        const size_t need = (size_t)2 * 8 * n_iter;
+        while (c->event_pool.size() < need) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            c->event_pool.push_back(ev);
+        }
+    }
+    long long before[KID_COUNT];
+    memcpy(before, c->launches, sizeof(before));
+    const size_t np0 = c->pending.size();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        c->capturing = true;
+        cudaError_t el = cudaSuccess;
+        for (int it = 0; it < n_iter && el == cudaSuccess; ++it) {
+            c->capture_iter = it;   // timing events on every 8th captured iteration
+            el = launch_iteration(c);
+        }
+        c->capturing = false;
+        e = cudaStreamEndCapture(c->stream, &g);
+        if (el != cudaSuccess) e = el;
+    }
+    for (int k = 0; k < KID_COUNT; ++k) {
+        c->iter_counts[k] = c->launches[k] - before[k];
+        c->launches[k] = before[k];
+    }
+    for (size_t p = np0; p < c->pending.size(); ++p) {
+        prof_rec r = c->pending[p];
+        r.graph_owned = true;
+        c->iter_prof.push_back(r);
+    }
+    c->pending.resize(np0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->iter_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->iter_exec = nullptr;
+        for (const prof_rec &r : c->iter_prof) {
+            c->event_pool.push_back(r.a);
+            c->event_pool.push_back(r.b);
+        }
+        c->iter_prof.clear();
+        c->iter_graph_failed = true;
+        return false;
+    }
+    c->iter_n = n_iter;
+    c->iter_mask = c->prof_mask;
+    c->iter_r = c->r;
+    c->iter_nused = c->n_used;
+    c->iter_T = c->d_T;
+    return true;
+}
+
 extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_info *info) {
     if (!c) return LRCCS_E_INVALID;
     if (!c->initialized) {
@@ -299,6 +395,16 @@ extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_i
         return LRCCS_E_INVALID;
     }
     int exited = 0;
+    // without the per-iteration exit test, replay the captured n-iteration graph
+    // (the same kernels, launched with fewer gaps); timing events, when
+    // requested, are nodes of the graph and report its latest replay
+    if (!c->prm.exit_enabled && n_iter > 1 && ensure_iter_graph(c, n_iter)) {
+        CK(cudaGraphLaunch(c->iter_exec, c->stream));
+        for (int k = 0; k < KID_COUNT; ++k) c->launches[k] += c->iter_counts[k];
+        c->pending.insert(c->pending.end(), c->iter_prof.begin(), c->iter_prof.end());
+        c->t += n_iter;
+        n_iter = 0;
+    }
     for (int it = 0; it < n_iter; ++it) {
         CK(launch_iteration(c));
         c->t += 1;
@@ -403,18 +509,27 @@ static cudaEvent_t get_event(lrccs_ctx *c) {
 
 void prof_begin(lrccs_ctx *c, int kid) {
     c->launches[kid] += 1;
-    if (c->prof_mask & (1ull << kid)) {
+    c->prof_this = (c->prof_mask & (1ull << kid)) && !(c->capturing && (c->capture_iter & 7) != 0);
+    if (c->prof_this) {
         prof_rec r;
         r.kid = kid;
+        r.graph_owned = false;
         r.a = get_event(c);
         r.b = get_event(c);
-        cudaEventRecord(r.a, c->stream);
+        // while the library captures its iteration graph the record must be
+        // External to become an event-record node (a plain record there only
+        // orders the capture); outside a capture it is a plain record
+        if (c->capturing) cudaEventRecordWithFlags(r.a, c->stream, cudaEventRecordExternal);
+        else cudaEventRecord(r.a, c->stream);
         c->pending.push_back(r);
     }
 }
 
 void prof_end(lrccs_ctx *c, int kid) {
-    if ((c->prof_mask & (1ull << kid)) && !c->pending.empty()) cudaEventRecord(c->pending.back().b, c->stream);
+    if (c->prof_this && !c->pending.empty()) {
+        if (c->capturing) cudaEventRecordWithFlags(c->pending.back().b, c->stream, cudaEventRecordExternal);
+        else cudaEventRecord(c->pending.back().b, c->stream);
+    }
 }
 
 static lrccs_status prof_fold(lrccs_ctx *c) {
@@ -424,9 +539,13 @@ static lrccs_status prof_fold(lrccs_ctx *c) {
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             c->prof_ms[r.kid] += ms;
             c->timed[r.kid] += 1;
+        } else {
+            cudaGetLastError();   // an unreadable pair is skipped, not reported later
         }
-        c->event_pool.push_back(r.a);
-        c->event_pool.push_back(r.b);
+        if (!r.graph_owned) {
+            c->event_pool.push_back(r.a);
+            c->event_pool.push_back(r.b);
+        }
     }
     c->pending.clear();
     return LRCCS_OK;

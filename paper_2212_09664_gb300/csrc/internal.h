@@ -45,6 +45,7 @@ extern const char *const kKernelNames[KID_COUNT];
 struct prof_rec {
     int kid;
     cudaEvent_t a, b;
+    bool graph_owned;   // recorded by nodes of the captured iteration graph
 };
 
 struct lrccs_ctx {
@@ -55,6 +56,20 @@ struct lrccs_ctx {
     unsigned long long prof_mask;
     std::vector<prof_rec> pending;
     std::vector<cudaEvent_t> event_pool;
+
+    // the n-iteration loop captured as a CUDA graph on `stream` and replayed by
+    // lrccs_iterate; rebuilt when the iteration count, the timed kernels or
+    // the shape it was captured for change
+    cudaGraphExec_t iter_exec;
+    long long iter_counts[KID_COUNT];   // kernel launches per replay
+    std::vector<prof_rec> iter_prof;    // timing events recorded by the graph
+    int iter_n, iter_r, iter_nused;
+    unsigned long long iter_mask;
+    const void *iter_T;
+    bool iter_graph_failed;             // capture not possible here: launch directly
+    bool capturing;                     // inside the library's own capture
+    int capture_iter;                   // iteration being captured
+    bool prof_this;                     // the current launch is timed
 
     lrccs_dims dims;
     lrccs_params prm;

@@ -229,3 +229,28 @@ def test_images_match_factors():
     X = s.images().cpu().numpy()        # (q, n): row k = x_k
     assert nrmse(X.T, g["X"][-1]) < 1e-6
     s.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    """lrccs_iterate(n > 1) on a created stream replays a captured graph of the n
+    iterations; it must give bit-identical factors to the same iterations
+    launched one call at a time, on its first replay and on a second one."""
+    p = synth.make_problem(MEDIUM, seed=12)
+    stream = torch.cuda.Stream(device=DEV)
+    a = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    b = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    inputs = to_dev(p)
+    a.init(*inputs)
+    b.init(*inputs)
+    for rounds in (1, 2):
+        a.iterate(8)                      # graph: captured on the first call, replayed on the second
+        for _ in range(8):
+            b.iterate(1)                  # one iteration per call: launched directly
+        Ua, Ba = a.factors()
+        Ub, Bb = b.factors()
+        torch.cuda.synchronize()
+        assert torch.equal(Ua, Ub) and torch.equal(Ba, Bb), "round %d" % rounds
+    ia, ib = a.iterate(1, info=True), b.iterate(1, info=True)
+    assert ia["t"] == ib["t"] == 17 and ia["sd"] == ib["sd"]
+    a.close()
+    b.close()
