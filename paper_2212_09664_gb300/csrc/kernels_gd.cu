@@ -215,6 +215,7 @@ struct Tile {
     int xs, ys, x0, x1, y0, y1;
 };
 static __device__ void tile_accumulate(const Tile &g, float2 (&acc)[4], int s, int S, int cn) {
+#pragma unroll 4
     for (int ii = s; ii < cn; ii += S) {
         const float2 p0 = g.X[ii * g.xs + g.x0], p1 = g.X[ii * g.xs + g.x1];
         const float2 q0 = g.Y[ii * g.ys + g.y0], q1 = g.Y[ii * g.ys + g.y1];
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             for (int l = 0; l < R; ++l) g0[l] = g1v[l] = make_float2(0.f, 0.f);
             const float2 *z0r = s_z + p0 * zs, *z1r = s_z + p1 * zs;
             int k = k0;
+#pragma unroll(R <= 12 ? 2 : 1)
             for (; k + 1 < k1; k += 2) {
                 const float4 za = *(const float4 *)(z0r + k), zb = *(const float4 *)(z1r + k);
 #pragma unroll
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             if (iter) a.Uprev[(size_t)c0 * r + e] = s_u[e];
         }
         if (hthr) {
+#pragma unroll(R <= 12 ? 2 : 1)
             for (int ii = hs; ii < cn; ii += Sh) {
                 const float4 z = *(const float4 *)(s_z + ii * zs + hk);   // Z[k], Z[k+1] (pad column when k+1 = q)
                 const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
@@ -547,6 +550,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
                 }
             }
         } else if (cthr) {
+#pragma unroll(R <= 12 ? 2 : 1)
             for (int ii = cs; ii < cn; ii += Sc) {
                 const float2 ux = s_u[ii * r + cx];
 #pragma unroll

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(256) k_row_gram(const float2 *__restrict__ T, 
         }
         __syncthreads();
         if (sl < S) {
+#pragma unroll 4
             for (int x = sl; x < nx; x += S) {
                 const float2 p0 = tile[x * R + x0], p1 = tile[x * R + x1];
                 const float2 q0 = tile[x * R + y0], q1 = tile[x * R + y1];
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
         }
         float2 *row = row0 + (size_t)j * plane;
         if (xg < NXG) {   // thread = (output column wb, x group): W_ky[:, wb] in registers
+#pragma unroll 2
             for (int x = xg; x < nx; x += NXG) {
                 const float2 *fr = tile + x * R;
                 float2 o = make_float2(0.f, 0.f);
