@@ -512,7 +512,7 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     const int v_in_smem = (size_t)2 * q * ld * sizeof(float2) + 4096 <= (size_t)c->dev_smem_optin;
     const size_t smem2 = (size_t)(v_in_smem ? 2 : 1) * q * ld * sizeof(float2);
     prof_begin(c, KID_EIG);
-    k_eig<<<1, 512, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
+    k_eig<<<1, 1024, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
                                         c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem);
     prof_end(c, KID_EIG);
     return cudaGetLastError();
