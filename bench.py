@@ -9,6 +9,11 @@ Metric: frame-iterations/s = q * 50 / (step time), whole job over all ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrccs|reference]
 
+After the timed solves (N = 1 only) a serving leg runs mini-batch subspace
+tracking (Alg. 4) as a real-time request loop over 8 acquisitions and reports
+the p50/p99 arrival-to-reconstruction latency of its mini-batches
+(--no-serving skips it).
+
 --impl reference times the FP64 CPU oracle (the only reference this work has)
 on a bounded sample of the same workload and extrapolates to a 50-iteration
 solve.  Under torchrun (N > 1) every rank solves its own replica of the
@@ -187,6 +192,147 @@ def cpu_baseline(p, y_ref_X2):
                        "extrapolated as t_init + %d t_iter" % (WORKLOAD, t2 - t0, T_ITER, T_ITER)), nrmse
 
 
+# Serving form of Alg. 4: mini-batch subspace tracking as a request loop.
+SERVE_STREAMS = 8          # acquisitions tracked at once, one client context pair each
+SERVE_FIRST = 32           # frames of the first mini-batch (Alg. 4 step 1, T_max,1 = 70)
+SERVE_ALPHA = 8            # frames of every later mini-batch (T_max,j = 5)
+SERVE_BATCHES = 12         # later mini-batches per acquisition
+SERVE_FPS = 20.0           # frame arrival rate per acquisition
+SERVE_STAGGER_S = 0.05     # acquisition i starts i x 50 ms after acquisition 0
+T_FIRST, T_NEXT = 70, 5
+
+
+def serving(dev):
+    """p50/p99 arrival-to-reconstruction latency of mini-batch subspace tracking.
+
+    Frames of every acquisition arrive in real time at SERVE_FPS.  When the last
+    frame of a mini-batch has arrived, its samples are copied from pinned host
+    memory, the mini-batch is solved on that acquisition's own stream (first
+    mini-batch: lrccs_init + lrccs_iterate(70); later ones:
+    lrccs_track_minibatch with 5 iterations, U kept on the device) and its images
+    are copied back to pinned host memory; the latency runs from the arrival of
+    that last frame to the moment the host sees the images.  One host thread
+    submits every request and polls for completions, so requests of different
+    acquisitions overlap on the GPU.  Every acquisition replays the same
+    synthetic sequence, so every client's images must equal, bit for bit, those
+    of one client run alone."""
+    import numpy as np
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs, synth
+
+    F1, A, M, S = SERVE_FIRST, SERVE_ALPHA, SERVE_BATCHES, SERVE_STREAMS
+    seq = synth.make_problem(WORKLOAD, seed=0x5EED0005, q=F1 + A * M)
+    parts = [synth.frames(seq, 0, F1)] + [synth.frames(seq, F1 + A * j, A) for j in range(M)]
+    host = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (b.y, b.frame_ptr, b.mask))
+            for b in parts]
+    smaps = torch.from_numpy(seq.smaps).to(dev)
+    n, r = seq.n, seq.rank
+
+    class Client:
+        def __init__(self):
+            self.stream = torch.cuda.Stream(device=dev)
+            self.first = lrccs.Solver(seq.ny, seq.nx, F1, seq.nc, r, stream=self.stream)
+            self.mb = lrccs.Solver(seq.ny, seq.nx, A, seq.nc, r, stream=self.stream)
+            with torch.cuda.stream(self.stream):
+                self.dev = [tuple(torch.empty_like(h, device=dev) for h in hb) for hb in host]
+                self.X = [torch.empty((b.q, n), dtype=torch.complex64, device=dev) for b in parts]
+                self.U = torch.empty((n, r), dtype=torch.complex64, device=dev)
+            self.Xh = torch.empty((F1, n), dtype=torch.complex64).pin_memory()
+            self.ready = False
+
+        def submit(self, j):
+            y, fp, mask = self.dev[j]
+            with torch.cuda.stream(self.stream):
+                for d, h in zip(self.dev[j], host[j]):
+                    d.copy_(h, non_blocking=True)
+                if j == 0:
+                    lrccs.lrccs_init(self.first.ctx, y, fp, mask, smaps)
+                    lrccs.lrccs_iterate(self.first.ctx, T_FIRST)
+                    lrccs.lrccs_get_images(self.first.ctx, self.X[0])
+                else:
+                    lrccs.lrccs_track_minibatch(self.mb.ctx, y, fp, mask, smaps, T_NEXT, False, self.X[j])
+                self.Xh[: parts[j].q].copy_(self.X[j], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+            return ev
+
+        def done(self, j):
+            ctx = self.first.ctx if j == 0 else self.mb.ctx
+            lrccs.lrccs_synchronize(ctx)      # raises on a device-side failure
+            if j == 0:                        # hand U^(1) and eta to the tracking context
+                eta = lrccs.lrccs_iterate(self.first.ctx, 0, info=True)["eta"]
+                lrccs.lrccs_get_subspace(self.first.ctx, self.U)
+                lrccs.lrccs_set_subspace(self.mb.ctx, self.U, r, eta)
+                self.ready = True
+
+        def close(self):
+            self.first.close()
+            self.mb.close()
+
+    # one client alone, back to back: the reference images, and the last
+    # mini-batch against the FP64 oracle from the same warm start
+    solo = Client()
+    for j in range(M + 1):
+        if j == M:
+            lrccs.lrccs_get_subspace(solo.mb.ctx, solo.U)
+            solo.stream.synchronize()
+            U_prev = solo.U.cpu().numpy().astype(np.complex128)
+            eta = lrccs.lrccs_iterate(solo.mb.ctx, 0, info=True)["eta"]
+        solo.submit(j).synchronize()
+        solo.done(j)
+    check = (parts[M], U_prev, eta, solo.X[M].cpu().numpy().astype(np.complex128))
+
+    clients = [Client() for _ in range(S)]
+    torch.cuda.synchronize()
+    events = sorted((i * SERVE_STAGGER_S + (F1 + A * j) / SERVE_FPS, i, j) for i in range(S) for j in range(M + 1))
+    lat = {}
+    pending = []
+    t0 = time.perf_counter() + 0.05
+
+    def poll():
+        for item in list(pending):
+            ev, i, j, ta = item
+            if ev.query():
+                lat[(i, j)] = time.perf_counter() - t0 - ta
+                pending.remove(item)
+                clients[i].done(j)
+
+    for ta, i, j in events:
+        while time.perf_counter() - t0 < ta or (j > 0 and not clients[i].ready):
+            poll()
+            if not pending:
+                time.sleep(max(0.0, min(2e-4, ta - (time.perf_counter() - t0))))
+        pending.append((clients[i].submit(j), i, j, ta))
+    while pending:
+        poll()
+    torch.cuda.synchronize()
+    same = all(torch.equal(c.X[j], solo.X[j]) for c in clients for j in range(M + 1))
+    later = np.array([lat[(i, j)] for i in range(S) for j in range(1, M + 1)]) * 1e3
+    firsts = np.array([lat[(i, 0)] for i in range(S)]) * 1e3
+    for c in clients + [solo]:
+        c.close()
+    return dict(streams=S, first_batch_frames=F1, t_first=T_FIRST, minibatch_frames=A, t_next=T_NEXT,
+                minibatches_per_stream=M, fps_per_stream=SERVE_FPS,
+                p50_ms=float(np.percentile(later, 50)), p99_ms=float(np.percentile(later, 99)),
+                max_ms=float(later.max()), first_batch_p50_ms=float(np.percentile(firsts, 50)),
+                first_batch_max_ms=float(firsts.max()), same_alone_and_in_mix=bool(same),
+                workload="%s-shaped acquisition of %d frames (one synthetic sequence replayed by every stream, "
+                         "starts staggered by %.0f ms)" % (WORKLOAD, F1 + A * M, SERVE_STAGGER_S * 1e3)), check
+
+
+def serving_parity(part, U_prev, eta, X_gpu):
+    """NRMSE of one tracked mini-batch's images against the FP64 oracle run from the
+    same warm start U^(j-1) and step size (part of the CPU-baseline leg)."""
+    import numpy as np
+
+    import oracle
+
+    ref = oracle.Operator.from_problem(part).iterate(part.y, U_prev, T_NEXT, eta=eta)
+    Xo = ref["Uprev"] @ ref["B"]
+    return float(np.linalg.norm(X_gpu.T - Xo) / np.linalg.norm(Xo))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lrccs", choices=["lrccs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the mini-batch tracking latency leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -341,6 +488,14 @@ def main():
                                      ms_per_iteration=(tot_ms - init_ms) / args.steps / T_ITER),
                 init_ms_per_solve=init_ms / args.steps,
                 p99_minibatch_latency_ms=None)
+    sv_check = None
+    if ws == 1 and not args.no_serving:
+        try:
+            sv, sv_check = serving(dev)
+            line["p99_minibatch_latency_ms"] = sv["p99_ms"]
+            line["serving"] = sv
+        except Exception as e:        # the solve's line is still printed; the failure is reported in it
+            line["serving"] = dict(error="%s: %s" % (type(e).__name__, e))
     if ws == 1 and not args.no_cpu_baseline:
         # X_2 of the GPU for the parity figure reported beside the oracle timing
         lrccs.lrccs_init(s.ctx, y, fp, mask, sm)
@@ -350,6 +505,8 @@ def main():
         cb, nr = cpu_baseline(p, X2)
         line["cpu_baseline"] = cb
         line["nrmse_x2_vs_fp64"] = nr
+        if sv_check is not None:
+            line["serving"]["nrmse_last_minibatch_vs_fp64"] = serving_parity(*sv_check)
     s.close()
     print(json.dumps(line), flush=True)
     if dist is not None:

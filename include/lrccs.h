@@ -89,7 +89,9 @@ typedef struct lrccs_iter_info {
 /* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off). */
 void lrccs_default_params(lrccs_params *p);
 
-/* Create a context for one problem size on the current CUDA device.
+/* Create a context for one problem size on the current CUDA device.  The rank
+ * may exceed q (a context that tracks mini-batches of fewer than r frames);
+ * lrccs_init then refuses the fixed rank.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  Allocates every
  * device buffer the solve needs.  Errors: LRCCS_E_INVALID (dims outside scope),
  * LRCCS_E_NOMEM, LRCCS_E_CUDA. */
@@ -106,7 +108,8 @@ lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params,
  * Compacts the masks, computes gamma, Z = [A_k^H y_k] and the truncated and
  * scaled X0, its top-r left singular vectors U_0, and resets t and eta.  The
  * call blocks until the device work is done.  Inputs are not retained.
- * Errors: LRCCS_E_INVALID (frame_ptr inconsistent with the mask),
+ * Errors: LRCCS_E_INVALID (frame_ptr inconsistent with the mask, or a fixed
+ * rank above q: the top-r singular vectors of the n x q X0 need r <= q),
  * LRCCS_E_UNSUPPORTED (a mask that is not a union of full lines),
  * LRCCS_E_RANK_DEFICIENT (sigma_r(X0) = 0), LRCCS_E_CUDA. */
 lrccs_status lrccs_init(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
@@ -132,7 +135,8 @@ lrccs_status lrccs_iterate(lrccs_ctx *ctx, int32_t n_iter, lrccs_iter_info *info
  * Before any iteration, d_U receives U_0 and d_B is left untouched. */
 lrccs_status lrccs_get_factors(lrccs_ctx *ctx, void *d_U, void *d_B);
 
-/* Current subspace estimate U_t (n x r), the input of the next iteration. */
+/* Current subspace estimate U_t (n x r, row-major), the input of the next
+ * iteration; also a subspace set by lrccs_set_subspace or lrccs_set_state. */
 lrccs_status lrccs_get_subspace(lrccs_ctx *ctx, void *d_U);
 
 /* Materialise X = U_{t-1} B_t into d_X (n x q column-major complex64). */
@@ -151,6 +155,86 @@ typedef enum lrccs_buffer {
     LRCCS_BUF_IDX = 4, LRCCS_BUF_SCAL = 5
 } lrccs_buffer;
 lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, size_t bytes);
+
+/* ---- Mini-batch subspace tracking (Alg. 4) ----------------------------------
+ * Alg. 4 reconstructs a long acquisition one mini-batch of consecutive frames
+ * at a time.  The first mini-batch (alpha_1 frames) is an ordinary solve:
+ * lrccs_init then lrccs_iterate (T_max,1 = 70 in the paper) on a context
+ * created with q = alpha_1.  Every later mini-batch j replaces the
+ * initialisation of Alg. 2 (gamma, truncation, X0 and its SVD) by
+ * U_0 <- U^(j-1), the final subspace of mini-batch j - 1, and runs at most
+ * T_max,j GDmin iterations (5 in the paper) on its own frames.  One context
+ * created with q = alpha tracks all later mini-batches of an acquisition:
+ * U stays in its device memory from one call to the next.
+ *
+ * Step size.  The paper sets eta = eta_c / ||grad||_2 at t = 1 from the
+ * initial estimates and relies on the gradient norm only decreasing after
+ * that (Sec. III-C).  Tracking calls therefore keep the step size in force,
+ * the one set at the first mini-batch's first iteration, unless reset_eta
+ * asks for it to be set again from the warm start's own first gradient
+ * (which, near convergence, is small: the first step then has spectral norm
+ * eta_c in a poorly determined direction). */
+
+/* Set the context's subspace and, optionally, its step size:
+ *   d_U  : device complex64, n x rank, row-major (element (i, l) at i * rank + l),
+ *          orthonormal columns; caller-owned, copied on the context's stream
+ *          (not retained).  The next iteration re-orthonormalises it by one
+ *          Cholesky QR pass (which changes an orthonormal U only by rounding)
+ *          and forms its first right-hand sides U^H Z from the data then loaded.
+ *   rank : 1 <= rank <= the context's rank_max; becomes the context's r
+ *   eta  : > 0: the GD step size from the next iteration on;
+ *          <= 0: set at the next iteration, eta = eta_c / ||grad||_2
+ * Hands the first mini-batch's U^(1) (lrccs_get_subspace) and eta (from
+ * lrccs_iterate's info) to the context that tracks the later mini-batches.
+ * The call synchronises the context's stream.
+ * Errors: LRCCS_E_INVALID (null pointer, rank out of range), LRCCS_E_CUDA. */
+lrccs_status lrccs_set_subspace(lrccs_ctx *ctx, const void *d_U, int32_t rank, double eta);
+
+/* Track one later mini-batch (Alg. 4, j > 1): U_0 <- the context's subspace,
+ * then t_max GDmin iterations of Alg. 2 on this mini-batch's q frames.
+ *   d_y, d_frame_ptr, d_mask : the mini-batch's samples, offsets and masks,
+ *          laid out as for lrccs_init (q = the context's q); caller-owned
+ *   d_smaps  : device complex64, C x n coil maps (copied)
+ *   t_max    : iterations, >= 1 (with exit_enabled the loop also stops once
+ *              SD(U_{t-1}, U_t) / sqrt(r) < eps_exit)
+ *   reset_eta: 0 keeps the step size in force; 1 sets it again at this
+ *              mini-batch's first iteration
+ *   d_X      : NULL, or device memory for this mini-batch's images
+ *              X = U_{t-1} B_t, q x n complex64 (row k = x_k), written
+ *              asynchronously
+ *   info     : NULL, or receives t, eta, sd, gnorm (the call then waits for
+ *              the iterations)
+ * The masks are compacted first (one wait for that step); the rest is queued
+ * on the context's stream and the call returns: lrccs_synchronize waits for it
+ * and reports its device status.  Afterwards the context holds this
+ * mini-batch's data and final subspace, so lrccs_iterate, lrccs_get_factors
+ * and lrccs_get_images work on it as after lrccs_init.  The iterations are
+ * the ones lrccs_iterate launches; a captured iteration graph is replayed only
+ * when it matches this mini-batch's sampled rows (none is captured here).
+ * Errors: LRCCS_E_STATE (no subspace: call lrccs_init, lrccs_set_subspace or
+ * lrccs_set_state first), LRCCS_E_INVALID, LRCCS_E_UNSUPPORTED (a mask that is
+ * not a union of full lines), LRCCS_E_RANK_DEFICIENT, LRCCS_E_TIMEOUT,
+ * LRCCS_E_CUDA. */
+lrccs_status lrccs_track_minibatch(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
+                                   const uint8_t *d_mask, const void *d_smaps, int32_t t_max,
+                                   int32_t reset_eta, void *d_X, lrccs_iter_info *info);
+
+/* Checkpoint and resume of the solver state that later iterations depend on:
+ * ny, nx, the rank r, the iteration count t, the step size eta (and whether it
+ * is set) and the subspace U_t, as one host byte buffer (a 64-byte header
+ * followed by U, n x r complex64).  The data (Z, masks) is not part of it.
+ *   lrccs_get_state: host_buf NULL stores the size in *bytes; otherwise *bytes
+ *     is the buffer's capacity on entry and the size written on return.
+ *     Synchronises the context's stream.
+ *   lrccs_set_state: takes a buffer written by lrccs_get_state of a context
+ *     with the same ny and nx and r <= this context's rank_max, and
+ *     synchronises.  To resume a solve, lrccs_init the same data, then
+ *     lrccs_set_state, then lrccs_iterate; to resume tracking, lrccs_set_state
+ *     then lrccs_track_minibatch.
+ * Errors: LRCCS_E_STATE (get: no subspace yet), LRCCS_E_INVALID (null
+ * pointer, short buffer, foreign or mismatched header), LRCCS_E_CUDA. */
+lrccs_status lrccs_get_state(lrccs_ctx *ctx, void *host_buf, size_t *bytes);
+lrccs_status lrccs_set_state(lrccs_ctx *ctx, const void *host_buf, size_t bytes);
 
 /* Kernel profiling (measurement support; the paper reports per-step timing
  * markers, Sec. V).  Launch counts of every kernel are kept always.  CUDA-event

@@ -219,6 +219,34 @@ class Operator:
         return out
 
 
+def track_minibatches(batches, rank, t_first=70, t_next=5, params: Params = None, reset_eta=False,
+                      U_start=None, eta_start=0.0):
+    """Mini-batch subspace tracking (Alg. 4) over `batches`, a list of
+    (Operator, y) pairs, one per mini-batch in arrival order.
+
+    The first mini-batch is solved by Alg. 2 (spectral initialisation, then
+    t_first GDmin iterations) unless U_start is given; every later one (and
+    the first, when U_start is given) starts from the previous final subspace,
+    U_0 <- U^(j-1), and runs t_next GDmin iterations.  The step size is the one
+    set at the first mini-batch's first iteration (or eta_start when > 0) and
+    is kept; reset_eta sets it again at every mini-batch's first iteration.
+    Returns one dict per mini-batch: X = U_{t-1} B_t (n x q_j), U (final),
+    eta, sd, gnorm, iters."""
+    params = params or Params()
+    out = []
+    U, eta = U_start, float(eta_start)
+    for j, (op, y) in enumerate(batches):
+        if U is None:
+            ini = op.init(y, params, rank=rank)
+            res = op.iterate(y, ini["U0"], t_first, params)
+        else:
+            res = op.iterate(y, U, t_next, params, eta=0.0 if reset_eta else eta)
+        U, eta = res["U"], res["eta"]
+        out.append(dict(X=res["Uprev"] @ res["B"], U=U, eta=eta, sd=res["sd"], gnorm=res["gnorm"],
+                        iters=res["iters"]))
+    return out
+
+
 def dft2(x, sign=-1) -> np.ndarray:
     x = _c128(x)
     ny, nx = x.shape

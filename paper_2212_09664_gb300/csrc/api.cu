@@ -98,10 +98,10 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     const lrccs_dims d = *dims;
     int rmax = d.rank_max > 0 ? d.rank_max : (d.rank > 0 ? d.rank : 16);
     if (!pow_ok(d.ny) || !pow_ok(d.nx) || d.q < 1 || d.q > 128 || d.ncoil < 1 || d.ncoil > 64 || d.rank < 0 ||
-        d.rank > 16 || rmax < 1 || rmax > 16 || (d.rank > 0 && d.rank > rmax) || (d.rank > d.q)) {
+        d.rank > 16 || rmax < 1 || rmax > 16 || (d.rank > 0 && d.rank > rmax)) {
         set_err(nullptr,
                 "lrccs_create: dims outside scope (ny, nx multiples of 32 in [32,256]; q in [1,128]; "
-                "ncoil in [1,64]; 0 <= rank <= rank_max <= 16; rank <= q)");
+                "ncoil in [1,64]; 0 <= rank <= rank_max <= 16)");
         return LRCCS_E_INVALID;
     }
     lrccs_ctx *c = new (std::nothrow) lrccs_ctx();
@@ -171,6 +171,8 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_meta, 0, ((size_t)MT_COUNT + q) * sizeof(int32_t), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         set_err(nullptr, "lrccs_create: %s", cudaGetErrorString(e));
@@ -235,18 +237,14 @@ static lrccs_status sync_status(lrccs_ctx *c) {
     return status_to_code(c, st);
 }
 
-extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr, const uint8_t *d_mask,
-                                   const void *d_smaps, int32_t *out_rank) {
-    if (!c) return LRCCS_E_INVALID;
-    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps) {
-        set_err(c, "lrccs_init: null input pointer");
-        return LRCCS_E_INVALID;
-    }
-    c->initialized = 0;
-    c->t = 0;
+// Mask compaction, the sampled-row structure and Z = [A_k^H y_k] for the data
+// of one lrccs_init or tracking call; with_energy also forms gamma, which only
+// the spectral initialisation's truncation uses.  Waits once, for the
+// compaction's counts.
+static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr, const uint8_t *d_mask,
+                              const void *d_smaps, bool with_energy) {
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream));
-    CK(cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->d_meta, 0, MT_COUNT * sizeof(int32_t), c->stream));
     CK(cudaMemcpyAsync(c->d_smaps, d_smaps, (size_t)c->nc * c->n * sizeof(float2), cudaMemcpyDeviceToDevice,
                        c->stream));
@@ -259,7 +257,7 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     c->n_lines = meta[MT_NLINES];
     c->total = (int64_t)c->n_lines * c->nx;
     if (c->total == 0 || c->n_used == 0) {
-        set_err(c, "lrccs_init: no sampled k-space");
+        set_err(c, "no sampled k-space");
         return LRCCS_E_INVALID;
     }
     const size_t need = (size_t)2 * c->nc * c->total;
@@ -272,11 +270,33 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
         }
         c->T_cap = need;
     }
-    CK(launch_energy(c, (const float2 *)d_y));
+    if (with_energy) CK(launch_energy(c, (const float2 *)d_y));
     CK(launch_init_adjoint(c, (const float2 *)d_y));
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr, const uint8_t *d_mask,
+                                   const void *d_smaps, int32_t *out_rank) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps) {
+        set_err(c, "lrccs_init: null input pointer");
+        return LRCCS_E_INVALID;
+    }
+    if (c->dims.rank > c->q) {   // U_0 = top-r left singular vectors of the n x q X0
+        set_err(c, "lrccs_init: rank %d above q = %d (the spectral initialisation needs r <= q)", c->dims.rank, c->q);
+        return LRCCS_E_INVALID;
+    }
+    c->initialized = 0;
+    c->has_u = 0;
+    c->need_h = 0;
+    c->t = 0;
+    CK(cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream));
+    lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, true);
+    if (s != LRCCS_OK) return s;
     CK(launch_gram_x0(c));
     s = sync_status(c);
     if (s != LRCCS_OK) return s;
+    int32_t meta[MT_COUNT];
     CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
     c->r = meta[MT_RANK];
     if (c->r < 1 || c->r > c->rmax) {
@@ -290,7 +310,20 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     s = sync_status(c);
     if (s != LRCCS_OK) return s;
     c->initialized = 1;
+    c->has_u = 1;
     if (out_rank) *out_rank = c->r;
+    return LRCCS_OK;
+}
+
+// U_0 <- the subspace in d_U (set from outside, or the previous mini-batch's
+// final U): one Cholesky QR pass of it (the init mode of k_gdqr, which also
+// forms the first B-step's right-hand sides U^H Z from the data now loaded).
+static lrccs_status warm_start(lrccs_ctx *c) {
+    const size_t ub = (size_t)c->n * c->r * sizeof(float2);
+    CK(cudaMemcpyAsync(c->d_Up, c->d_U, ub, cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_gdqr(c, 0));
+    CK(cudaMemcpyAsync(c->d_Uprev, c->d_U, ub, cudaMemcpyDeviceToDevice, c->stream));
+    c->need_h = 0;
     return LRCCS_OK;
 }
 
@@ -311,11 +344,14 @@ static void drop_iter_graph(lrccs_ctx *c) {
     c->iter_prof.clear();
 }
 
+static bool graph_matches(const lrccs_ctx *c, int n_iter) {
+    return c->iter_exec && c->iter_n == n_iter && c->iter_mask == c->prof_mask && c->iter_r == c->r &&
+           c->iter_nused == c->n_used && c->iter_T == c->d_T;
+}
+
 static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
     if (c->iter_graph_failed) return false;
-    if (c->iter_exec && c->iter_n == n_iter && c->iter_mask == c->prof_mask && c->iter_r == c->r &&
-        c->iter_nused == c->n_used && c->iter_T == c->d_T)
-        return true;
+    if (graph_matches(c, n_iter)) return true;
     if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread) {
         c->iter_graph_failed = true;
         return false;
@@ -384,21 +420,16 @@ static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
     return true;
 }
 
-extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_info *info) {
-    if (!c) return LRCCS_E_INVALID;
-    if (!c->initialized) {
-        set_err(c, "lrccs_iterate: call lrccs_init first");
-        return LRCCS_E_STATE;
-    }
-    if (n_iter < 0) {
-        set_err(c, "lrccs_iterate: n_iter < 0");
-        return LRCCS_E_INVALID;
-    }
+// n_iter iterations on the loaded data.  may_capture: build the iteration
+// graph when none matches (lrccs_iterate); otherwise replay one only when it
+// already matches (tracking calls, whose sampled rows change every call).
+static lrccs_status run_iterations(lrccs_ctx *c, int n_iter, bool may_capture, lrccs_iter_info *info) {
     int exited = 0;
     // without the per-iteration exit test, replay the captured n-iteration graph
     // (the same kernels, launched with fewer gaps); timing events, when
     // requested, are nodes of the graph and report its latest replay
-    if (!c->prm.exit_enabled && n_iter > 1 && ensure_iter_graph(c, n_iter)) {
+    if (!c->prm.exit_enabled && n_iter > 1 &&
+        (may_capture ? ensure_iter_graph(c, n_iter) : graph_matches(c, n_iter))) {
         CK(cudaGraphLaunch(c->iter_exec, c->stream));
         for (int k = 0; k < KID_COUNT; ++k) c->launches[k] += c->iter_counts[k];
         c->pending.insert(c->pending.end(), c->iter_prof.begin(), c->iter_prof.end());
@@ -434,10 +465,161 @@ extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_i
     return LRCCS_OK;
 }
 
-extern "C" lrccs_status lrccs_get_factors(lrccs_ctx *c, void *d_U, void *d_B) {
+extern "C" lrccs_status lrccs_iterate(lrccs_ctx *c, int32_t n_iter, lrccs_iter_info *info) {
     if (!c) return LRCCS_E_INVALID;
     if (!c->initialized) {
-        set_err(c, "lrccs_get_factors: call lrccs_init first");
+        set_err(c, "lrccs_iterate: call lrccs_init first");
+        return LRCCS_E_STATE;
+    }
+    if (n_iter < 0) {
+        set_err(c, "lrccs_iterate: n_iter < 0");
+        return LRCCS_E_INVALID;
+    }
+    if (c->need_h && n_iter > 0) {
+        lrccs_status s = warm_start(c);
+        if (s != LRCCS_OK) return s;
+    }
+    return run_iterations(c, n_iter, true, info);
+}
+
+// ---------------------------------------------------------------- subspace tracking (Alg. 4)
+
+extern "C" lrccs_status lrccs_set_subspace(lrccs_ctx *c, const void *d_U, int32_t rank, double eta) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_U || rank < 1 || rank > c->rmax) {
+        set_err(c, "lrccs_set_subspace: need d_U and 1 <= rank <= rank_max (%d)", c->rmax);
+        return LRCCS_E_INVALID;
+    }
+    CK(cudaMemcpyAsync(c->d_U, d_U, (size_t)c->n * rank * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+    const double eta_v = eta > 0.0 ? eta : 0.0, set_v = eta > 0.0 ? 1.0 : 0.0, zero = 0.0;
+    CK(cudaMemcpyAsync(c->d_scal + SC_ETA, &eta_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_ETASET, &set_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_GNORM, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->r = rank;
+    c->t = 0;
+    c->has_u = 1;
+    c->need_h = 1;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_track_minibatch(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr,
+                                              const uint8_t *d_mask, const void *d_smaps, int32_t t_max,
+                                              int32_t reset_eta, void *d_X, lrccs_iter_info *info) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps || t_max < 1) {
+        set_err(c, "lrccs_track_minibatch: null input pointer or t_max < 1");
+        return LRCCS_E_INVALID;
+    }
+    if (!c->has_u) {
+        set_err(c, "lrccs_track_minibatch: no subspace (lrccs_init, lrccs_set_subspace or lrccs_set_state first)");
+        return LRCCS_E_STATE;
+    }
+    c->initialized = 0;
+    // Alg. 4: the initialisation of Alg. 2 is replaced by U_0 <- U^(j-1)
+    if (reset_eta) CK(cudaMemsetAsync(c->d_scal + SC_ETASET, 0, sizeof(double), c->stream));
+    lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, false);
+    if (s != LRCCS_OK) return s;
+    s = warm_start(c);
+    if (s != LRCCS_OK) return s;
+    c->t = 0;
+    c->initialized = 1;
+    s = run_iterations(c, t_max, false, info);
+    if (s != LRCCS_OK) return s;
+    if (d_X) CK(launch_images(c, (float2 *)d_X));
+    return LRCCS_OK;
+}
+
+// State buffer: this header, then U (n x r complex64).
+struct state_header {
+    uint32_t magic, version;
+    int32_t ny, nx, r, t, eta_set, reserved;
+    double eta, gnorm;
+    uint8_t pad[16];
+};
+static_assert(sizeof(state_header) == 64, "state header is 64 bytes");
+static const uint32_t kStateMagic = 0x5343524Cu;   // "LRCS"
+
+extern "C" lrccs_status lrccs_get_state(lrccs_ctx *c, void *host_buf, size_t *bytes) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!bytes) {
+        set_err(c, "lrccs_get_state: bytes must be non-null");
+        return LRCCS_E_INVALID;
+    }
+    if (!c->has_u) {
+        set_err(c, "lrccs_get_state: no subspace yet");
+        return LRCCS_E_STATE;
+    }
+    const size_t ub = (size_t)c->n * c->r * sizeof(float2);
+    const size_t need = sizeof(state_header) + ub;
+    if (!host_buf) {
+        *bytes = need;
+        return LRCCS_OK;
+    }
+    if (*bytes < need) {
+        set_err(c, "lrccs_get_state: buffer holds %zu bytes, %zu needed", *bytes, need);
+        return LRCCS_E_INVALID;
+    }
+    double sc[SC_COUNT];
+    CK(cudaMemcpyAsync(sc, c->d_scal, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync((char *)host_buf + sizeof(state_header), c->d_U, ub, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    state_header h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kStateMagic;
+    h.version = 1;
+    h.ny = c->ny;
+    h.nx = c->nx;
+    h.r = c->r;
+    h.t = c->t;
+    h.eta_set = sc[SC_ETASET] != 0.0 ? 1 : 0;
+    h.eta = sc[SC_ETA];
+    h.gnorm = sc[SC_GNORM];
+    memcpy(host_buf, &h, sizeof(h));
+    *bytes = need;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_set_state(lrccs_ctx *c, const void *host_buf, size_t bytes) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!host_buf || bytes < sizeof(state_header)) {
+        set_err(c, "lrccs_set_state: null or short buffer");
+        return LRCCS_E_INVALID;
+    }
+    state_header h;
+    memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1) {
+        set_err(c, "lrccs_set_state: not a state buffer of this library");
+        return LRCCS_E_INVALID;
+    }
+    if (h.ny != c->ny || h.nx != c->nx || h.r < 1 || h.r > c->rmax || h.t < 0) {
+        set_err(c, "lrccs_set_state: state of a %dx%d rank-%d solve does not fit this context (%dx%d, rank_max %d)",
+                h.ny, h.nx, h.r, c->ny, c->nx, c->rmax);
+        return LRCCS_E_INVALID;
+    }
+    const size_t ub = (size_t)c->n * h.r * sizeof(float2);
+    if (bytes < sizeof(state_header) + ub) {
+        set_err(c, "lrccs_set_state: buffer holds %zu bytes, %zu needed", bytes, sizeof(state_header) + ub);
+        return LRCCS_E_INVALID;
+    }
+    const double set_v = h.eta_set ? 1.0 : 0.0;
+    CK(cudaMemcpyAsync(c->d_U, (const char *)host_buf + sizeof(state_header), ub, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_ETA, &h.eta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_GNORM, &h.gnorm, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_ETASET, &set_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->r = h.r;
+    c->t = h.t;
+    c->has_u = 1;
+    c->need_h = 1;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_factors(lrccs_ctx *c, void *d_U, void *d_B) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!c->initialized || c->need_h) {
+        set_err(c, "lrccs_get_factors: no factors (call lrccs_init, or iterate after setting the subspace)");
         return LRCCS_E_STATE;
     }
     if (d_U)
@@ -450,8 +632,8 @@ extern "C" lrccs_status lrccs_get_factors(lrccs_ctx *c, void *d_U, void *d_B) {
 
 extern "C" lrccs_status lrccs_get_subspace(lrccs_ctx *c, void *d_U) {
     if (!c || !d_U) return LRCCS_E_INVALID;
-    if (!c->initialized) {
-        set_err(c, "lrccs_get_subspace: call lrccs_init first");
+    if (!c->has_u) {
+        set_err(c, "lrccs_get_subspace: no subspace yet");
         return LRCCS_E_STATE;
     }
     CK(cudaMemcpyAsync(d_U, c->d_U, (size_t)c->n * c->r * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
@@ -460,7 +642,7 @@ extern "C" lrccs_status lrccs_get_subspace(lrccs_ctx *c, void *d_U) {
 
 extern "C" lrccs_status lrccs_get_images(lrccs_ctx *c, void *d_X) {
     if (!c || !d_X) return LRCCS_E_INVALID;
-    if (!c->initialized || c->t == 0) {
+    if (!c->initialized || c->t == 0 || c->need_h) {
         set_err(c, "lrccs_get_images: run at least one iteration first");
         return LRCCS_E_STATE;
     }

@@ -76,7 +76,9 @@ struct lrccs_ctx {
     cudaStream_t stream;
     int ny, nx, n, q, nc, rmax;
     int r;             // rank in use (after init)
-    int initialized;   // lrccs_init succeeded
+    int initialized;   // data and subspace loaded (lrccs_init or a tracking call succeeded)
+    int has_u;         // d_U holds a subspace (init, lrccs_set_subspace, lrccs_set_state, tracking)
+    int need_h;        // d_U was set from outside: re-orthonormalise it and form U^H Z before iterating
     int t;             // iterations run since init
     int px, py;        // nx / 32, ny / 32
     int nblk;          // blocks of the pixel-parallel init kernels

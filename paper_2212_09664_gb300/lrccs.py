@@ -60,6 +60,10 @@ _sig = {
     "lrccs_profile_read": (_st, [_vp, C.POINTER(KernelStat), C.c_int32, C.POINTER(C.c_int32)]),
     "lrccs_profile_reset": (_st, [_vp]),
     "lrccs_trunc_threshold_noalloc": (_st, [_vp, C.c_int64, C.c_double, _vp, _vp]),
+    "lrccs_set_subspace": (_st, [_vp, _vp, C.c_int32, C.c_double]),
+    "lrccs_track_minibatch": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.POINTER(IterInfo)]),
+    "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
+    "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_destroy": (None, [_vp]),
     "lrccs_last_error": (C.c_char_p, [_vp]),
     "lrccs_status_string": (C.c_char_p, [_st]),
@@ -116,9 +120,7 @@ def lrccs_init(ctx, y, frame_ptr, mask, smaps) -> int:
 def lrccs_iterate(ctx, n_iter: int, info: bool = False):
     inf = IterInfo() if info else None
     _check(ctx, _lib.lrccs_iterate(ctx, int(n_iter), C.byref(inf) if info else None))
-    if info:
-        return dict(t=inf.t, exited=inf.exited, eta=inf.eta, sd=inf.sd, gnorm=inf.gnorm)
-    return None
+    return _info_dict(inf) if info else None
 
 
 def lrccs_get_factors(ctx, U=None, B=None):
@@ -173,6 +175,34 @@ def lrccs_trunc_threshold_noalloc(y, count, trunc_factor, gamma_out, stream=None
     _check(None, _lib.lrccs_trunc_threshold_noalloc(_ptr(y), int(count), float(trunc_factor), _ptr(gamma_out), s))
 
 
+def lrccs_set_subspace(ctx, U, rank: int, eta: float = 0.0):
+    _check(ctx, _lib.lrccs_set_subspace(ctx, _ptr(U), int(rank), float(eta)))
+
+
+def _info_dict(inf):
+    return dict(t=inf.t, exited=inf.exited, eta=inf.eta, sd=inf.sd, gnorm=inf.gnorm)
+
+
+def lrccs_track_minibatch(ctx, y, frame_ptr, mask, smaps, t_max: int, reset_eta: bool = False, X=None,
+                          info: bool = False):
+    inf = IterInfo() if info else None
+    _check(ctx, _lib.lrccs_track_minibatch(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps), int(t_max),
+                                           1 if reset_eta else 0, _ptr(X), C.byref(inf) if info else None))
+    return _info_dict(inf) if info else None
+
+
+def lrccs_get_state(ctx) -> bytes:
+    n = C.c_size_t(0)
+    _check(ctx, _lib.lrccs_get_state(ctx, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, _lib.lrccs_get_state(ctx, buf, C.byref(n)))
+    return buf.raw[: n.value]
+
+
+def lrccs_set_state(ctx, state: bytes):
+    _check(ctx, _lib.lrccs_set_state(ctx, state, len(state)))
+
+
 def lrccs_last_error(ctx=None) -> str:
     return (_lib.lrccs_last_error(ctx) or b"").decode()
 
@@ -210,6 +240,25 @@ class Solver:
 
     def iterate(self, n_iter, info=False):
         return lrccs_iterate(self.ctx, n_iter, info)
+
+    def set_subspace(self, U, eta=0.0):
+        """U_0 <- U (n x r) for the next tracking call or iteration; eta > 0 fixes the step size."""
+        lrccs_set_subspace(self.ctx, U, U.shape[1], eta)
+        self.r = U.shape[1]
+
+    def track(self, y, frame_ptr, mask, smaps, t_max=5, reset_eta=False, X=None, info=False):
+        """One later mini-batch of Alg. 4 (warm start, t_max iterations).  X: optional
+        (q, n) complex64 output, row k = x_k.  Returns the info dict when info=True."""
+        return lrccs_track_minibatch(self.ctx, y, frame_ptr, mask, smaps, t_max, reset_eta, X, info)
+
+    def get_state(self) -> bytes:
+        return lrccs_get_state(self.ctx)
+
+    def set_state(self, state: bytes):
+        lrccs_set_state(self.ctx, state)
+        import struct
+
+        self.r = struct.unpack_from("<i", state, 16)[0]
 
     def factors(self):
         t = self._torch

@@ -258,6 +258,29 @@ class Problem:
         return self.y[a:a + self.nc * mk].reshape(self.nc, mk)
 
 
+def frames(p: Problem, start: int, count: int) -> Problem:
+    """The frames [start, start + count) of `p` as a problem of their own (the
+    same coil maps; masks, sample offsets, data and per-frame truth sliced).
+    Mini-batches of an acquisition (Alg. 4) are cut this way."""
+    if start < 0 or count < 1 or start + count > p.q:
+        raise ValueError("frames %d..%d outside 0..%d" % (start, start + count, p.q))
+    fp = p.frame_ptr
+    a, b = int(fp[start]), int(fp[start + count])
+    truth = {}
+    for k, v in p.truth.items():
+        if k == "spectra":
+            truth[k] = v[start:start + count]
+        elif k == "B":
+            truth[k] = v[:, start:start + count]
+        elif k == "y128":
+            truth[k] = v[p.nc * a: p.nc * b]
+        else:
+            truth[k] = v
+    return dataclasses.replace(p, name="%s[%d:%d]" % (p.name, start, start + count), q=count,
+                               mask=p.mask[start:start + count], idx=p.idx[a:b], frame_ptr=fp[start:start + count + 1] - a,
+                               y=p.y[p.nc * a: p.nc * b], truth=truth)
+
+
 def compact_mask(mask: np.ndarray):
     """Bitmap -> (idx int32 sorted per frame, frame_ptr int64)."""
     q = mask.shape[0]

@@ -68,7 +68,6 @@ def test_default_params_are_the_papers(lib):
     (64, 64, 0, 2, 2, 0),     # no frames
     (64, 64, 8, 2, 17, 0),    # rank above 16
     (64, 64, 8, 0, 2, 0),     # no coils
-    (64, 64, 4, 1, 5, 0),     # rank above q
     (512, 64, 8, 1, 2, 0),    # side above 256
 ])
 def test_create_rejects_dims_outside_scope(lib, dims):
@@ -85,3 +84,16 @@ def test_status_strings(lib):
 
     for s in range(9):
         assert lrccs._lib.lrccs_status_string(s)
+
+
+def test_null_context_is_rejected_before_any_device_work(lib):
+    """Every entry point that takes a context checks it before touching CUDA."""
+    from paper_2212_09664_gb300 import lrccs
+
+    L = lrccs._lib
+    n = C.c_size_t(0)
+    assert L.lrccs_iterate(None, 1, None) == lrccs.E_INVALID
+    assert L.lrccs_set_subspace(None, None, 1, 0.0) == lrccs.E_INVALID
+    assert L.lrccs_track_minibatch(None, None, None, None, None, 5, 0, None, None) == lrccs.E_INVALID
+    assert L.lrccs_get_state(None, None, C.byref(n)) == lrccs.E_INVALID
+    assert L.lrccs_set_state(None, b"x" * 64, 64) == lrccs.E_INVALID
