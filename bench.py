@@ -49,6 +49,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise maximum over all ranks of this rank's timings (ms); the
+    timings of one rank unchanged when there is no process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(ws, q, n_solves, total_ms):
+    """Frame-iterations/s of the whole job: every rank solves its own replica,
+    n_solves times, within total_ms (the slowest rank's time)."""
+    return ws * q * T_ITER * n_solves / (total_ms / 1e3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -451,14 +469,10 @@ def main():
     h2d = sum(t.numel() * t.element_size() for t in (y, fp, mask, sm))
     d2h = sum(t.numel() * t.element_size() for t in (U, B))
 
-    # max over ranks
-    if dist is not None:
-        tt = torch.tensor([tot_ms, e2e_ms, init_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms, e2e_ms, init_ms = float(tt[0]), float(tt[1]), float(tt[2])
+    tot_ms, e2e_ms, init_ms = max_over_ranks([tot_ms, e2e_ms, init_ms], dist, dev)
     work = ws * p.q * T_ITER
-    value = work * args.steps / (tot_ms / 1e3)
-    e2e_value = work * n_e2e / (e2e_ms / 1e3)
+    value = whole_job_rate(ws, p.q, args.steps, tot_ms)
+    e2e_value = whole_job_rate(ws, p.q, n_e2e, e2e_ms)
 
     if rank != 0:
         if dist is not None:
