@@ -12,7 +12,9 @@ Metric: frame-iterations/s = q * 50 / (step time), whole job over all ranks.
 After the timed solves (N = 1 only) a serving leg runs mini-batch subspace
 tracking (Alg. 4) as a real-time request loop over 8 acquisitions and reports
 the p50/p99 arrival-to-reconstruction latency of its mini-batches
-(--no-serving skips it).
+(--no-serving skips it), and cuFFT / cuBLAS versions of the transform and
+gradient-step products are timed beside the fused kernels (--no-comparators
+skips them).
 
 --impl reference times the FP64 CPU oracle (the only reference this work has)
 on a bounded sample of the same workload and extrapolates to a 50-iteration
@@ -339,6 +341,71 @@ def serving(dev):
                          "starts staggered by %.0f ms)" % (WORKLOAD, F1 + A * M, SERVE_STAGGER_S * 1e3)), check
 
 
+def library_comparators(p, dev, used_rows, stats):
+    """cuFFT and cuBLAS (through torch) versions of iteration steps, timed beside
+    the library's fused kernels on the same shapes.  Comparators only: nothing
+    here is on the solver's path.
+      forward : coil multiply d_j o U, FFT along ky (cuFFT), gather of the
+                sampled rows                         vs k_fwd_cols
+      adjoint : scatter of the sampled rows, inverse FFT along ky (cuFFT),
+                conj(d_j) multiply, coil sum          vs k_adj_cols
+      gemms   : the gradient step's skinny products Z B^H and U^H Z (cuBLAS)
+                vs k_gdqr, which also forms grad, the GD step and the QR
+    Times are CUDA-event averages over back-to-back launches (inputs resident,
+    as for the kernels' own event times taken during the warm-up solves)."""
+    import torch
+
+    C, r, ny, nx, q, n = p.nc, p.rank, p.ny, p.nx, p.q, p.n
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    S = torch.from_numpy(p.smaps).to(dev).reshape(C, ny, nx)
+    U = torch.randn((ny, nx, r), dtype=torch.complex64, device=dev, generator=gen)
+    Z = torch.randn((n, q), dtype=torch.complex64, device=dev, generator=gen)
+    Bm = torch.randn((q, r), dtype=torch.complex64, device=dev, generator=gen)
+    rows = torch.tensor(used_rows, dtype=torch.long, device=dev)
+    K = torch.randn((C, r, rows.numel(), nx), dtype=torch.complex64, device=dev, generator=gen)
+    full = torch.zeros((C, r, ny, nx), dtype=torch.complex64, device=dev)
+
+    def forward():
+        W = S[:, None] * U.permute(2, 0, 1)[None]
+        return torch.fft.fft(W, dim=2, norm="ortho").index_select(2, rows)
+
+    def adjoint():
+        full.index_copy_(2, rows, K)
+        G = torch.fft.ifft(full, dim=2, norm="ortho")
+        return (S.conj()[:, None] * G).sum(0)
+
+    def gemms():
+        return Z @ Bm.conj(), U.reshape(n, r).conj().transpose(0, 1) @ Z
+
+    def time_us(fn, reps=50):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e3
+
+    def ours_us(name):
+        d = [x for x in stats if x["name"] == name]
+        return d[0]["ms"] / d[0]["timed"] * 1e3 if d and d[0]["timed"] else None
+
+    out = dict(
+        forward=dict(library_us=time_us(forward), lrccs_kernel="k_fwd_cols", lrccs_us=ours_us("k_fwd_cols"),
+                     library="torch elementwise + cuFFT (torch.fft.fft) + index_select"),
+        adjoint=dict(library_us=time_us(adjoint), lrccs_kernel="k_adj_cols", lrccs_us=ours_us("k_adj_cols"),
+                     library="index_copy + cuFFT (torch.fft.ifft) + elementwise + sum"),
+        gemms=dict(library_us=time_us(gemms), lrccs_kernel="k_gdqr", lrccs_us=ours_us("k_gdqr"),
+                   library="cuBLAS (torch.matmul): Z B^H and U^H Z; k_gdqr also forms grad, the GD step and QR"))
+    del full, K, Z, U
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_parity(part, U_prev, eta, X_gpu):
     """NRMSE of one tracked mini-batch's images against the FP64 oracle run from the
     same warm start U^(j-1) and step size (part of the CPU-baseline leg)."""
@@ -359,6 +426,7 @@ def main():
     ap.add_argument("--impl", default="lrccs", choices=["lrccs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the mini-batch tracking latency leg")
+    ap.add_argument("--no-comparators", action="store_true", help="skip the cuFFT / cuBLAS comparator timings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -502,6 +570,12 @@ def main():
                                      ms_per_iteration=(tot_ms - init_ms) / args.steps / T_ITER),
                 init_ms_per_solve=init_ms / args.steps,
                 p99_minibatch_latency_ms=None)
+    if ws == 1 and not args.no_comparators:
+        try:
+            used = np.flatnonzero(p.mask.reshape(p.q, p.ny, p.nx)[:, :, 0].any(0)).tolist()
+            line["comparators"] = library_comparators(p, dev, used, stats)
+        except Exception as e:
+            line["comparators"] = dict(error="%s: %s" % (type(e).__name__, e))
     sv_check = None
     if ws == 1 and not args.no_serving:
         try:
