@@ -181,6 +181,40 @@ def test_bstep_is_pseudo_inverse_solution():
 
 
 @pytest.mark.parametrize("mask", ["lines", "scatter"])
+def test_cost_is_the_residual_norm_with_dense_operators(mask):
+    """f(U, B) = sum_k ||y_k - A_k U b_k||^2 with each A_k built explicitly."""
+    op, rng = small_mri(13, ny=8, nx=8, q=4, nc=2, mask=mask)
+    U = crandn(rng, op.n, 3)
+    B = crandn(rng, 3, op.q)
+    y = crandn(rng, int(op.nc * op._fp[-1]))
+    ref = 0.0
+    for k in range(op.q):
+        yk = y[op.nc * op._fp[k]: op.nc * op._fp[k + 1]]
+        ref += np.linalg.norm(yk - dense_A(op, k) @ (U @ B[:, k])) ** 2
+    assert abs(op.cost(y, U, B) - ref) < 1e-12 * ref
+
+
+def test_subspace_distance_principal_angles():
+    """SD(U1, U2) = ||(I - U1 U1^H) U2||_F = ||sin Theta||_F, and
+    SD^2 = r - sum_i cos^2 theta_i with cos theta_i the singular values of U1^H U2."""
+    rng = np.random.default_rng(14)
+    n, r = 40, 3
+    U1 = synth.random_orthonormal(rng, n, r)
+    U2 = synth.random_orthonormal(rng, n, r)
+    cos = np.linalg.svd(U1.conj().T @ U2, compute_uv=False)
+    assert abs(oracle.sd(U1, U2) - math.sqrt(r - np.sum(cos ** 2))) < 1e-13
+    Q = synth.random_orthonormal(rng, r, r)
+    assert oracle.sd(U1, U1 @ Q) < 1e-13                     # same subspace, another basis
+    W = synth.random_orthonormal(rng, n, 2 * r)              # two orthogonal subspaces
+    assert abs(oracle.sd(W[:, :r], W[:, r:]) - math.sqrt(r)) < 1e-13
+    # one basis vector turned by t towards an orthogonal direction: SD = |sin t|
+    t = 0.3
+    V = W[:, :r].copy()
+    V[:, 0] = math.cos(t) * W[:, 0] + math.sin(t) * W[:, r]
+    assert abs(oracle.sd(W[:, :r], V) - abs(math.sin(t))) < 1e-13
+
+
+@pytest.mark.parametrize("mask", ["lines", "scatter"])
 def test_gradient_central_differences(mask):
     """(f(U+eD,B) - f(U-eD,B))/2e = 2 Re tr(grad^H D) for f = sum_k ||y_k - A_k U b_k||^2."""
     op, rng = small_mri(11, ny=8, nx=8, q=4, nc=2, mask=mask)
