@@ -8,6 +8,7 @@ shares no code with the CUDA library.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -217,6 +218,48 @@ class Operator:
         if history:
             out["X"] = Xh[:t]
         return out
+
+
+def mean_step(op, y, tol=1e-3, maxit=10):
+    """Alg. 1 step 1: zbar = argmin_z sum_k ||y_k - A_k z||^2 by CGLS (conjugate
+    gradients on the normal equations A^H A z = A^H y of the stacked operator
+    A = [A_1; ...; A_q], started at z = 0), stopped after maxit iterations or
+    once ||A^H r_t|| <= tol ||A^H y||; then the residual measurements
+    y~_k = y_k - A_k zbar (Alg. 1 step 2a).  Returns dict(zbar, ytil, iters,
+    normal_res: ||A^H r_t|| for t = 0..iters)."""
+    y = _c128(y)
+    q = op.q
+
+    def A(z):
+        return np.concatenate([op.forward(k, z) for k in range(q)])
+
+    def AH(v):
+        out = np.zeros(op.n, dtype=np.complex128)
+        for k in range(q):
+            a = op.yoff(k)
+            out += op.adjoint(k, v[a: a + op.rows(k)])
+        return out
+
+    z = np.zeros(op.n, dtype=np.complex128)
+    res = y.copy()                      # r_0 = y - A z_0
+    s = AH(res)                         # normal residual A^H r
+    p = s.copy()
+    gamma = np.vdot(s, s).real
+    norms0 = math.sqrt(gamma)
+    hist = [norms0]
+    t = 0
+    while t < maxit and hist[-1] > tol * norms0 and norms0 > 0:
+        w = A(p)
+        alpha = gamma / np.vdot(w, w).real
+        z = z + alpha * p
+        res = res - alpha * w
+        s = AH(res)
+        gamma_new = np.vdot(s, s).real
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+        hist.append(math.sqrt(gamma))
+        t += 1
+    return dict(zbar=z, ytil=y - A(z), iters=t, normal_res=np.array(hist))
 
 
 def track_minibatches(batches, rank, t_first=70, t_next=5, params: Params = None, reset_eta=False,
