@@ -156,6 +156,27 @@ typedef enum lrccs_buffer {
 } lrccs_buffer;
 lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, size_t bytes);
 
+/* ---- Mean step (Alg. 1, steps 1 and 2a) -------------------------------------
+ * zbar = argmin_z sum_k ||y_k - A_k z||^2 by CGLS (conjugate gradients on the
+ * normal equations A^H A z = A^H y of the stacked A = [A_1; ...; A_q], from
+ * z = 0), stopped once ||A^H r_t|| <= tol ||A^H y|| or after max_iter
+ * iterations (the paper: tol 1e-3, 10 iterations), and the residual
+ * measurements y~_k = y_k - A_k zbar, which Alg. 1 passes to Alg. 2
+ * (lrccs_init with d_y = d_ytil).
+ *   d_y, d_frame_ptr, d_mask, d_smaps : as for lrccs_init
+ *   tol       : >= 0;  max_iter : 0 .. 10000
+ *   d_zbar    : device complex64, n entries (caller-owned), receives zbar
+ *   d_ytil    : NULL, or device complex64 laid out like d_y (C * fp[q]
+ *               entries, caller-owned, not aliasing d_y), receives y~
+ *   out_iters : NULL, or receives the number of CG iterations run
+ * The CG vectors use the context's subspace buffers, so afterwards the context
+ * holds no solve (lrccs_init starts one).  The call synchronises.
+ * Errors: LRCCS_E_INVALID, LRCCS_E_UNSUPPORTED (a mask that is not a union of
+ * full lines), LRCCS_E_CUDA. */
+lrccs_status lrccs_mean_step(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
+                             const uint8_t *d_mask, const void *d_smaps, double tol, int32_t max_iter,
+                             void *d_zbar, void *d_ytil, int32_t *out_iters);
+
 /* ---- Mini-batch subspace tracking (Alg. 4) ----------------------------------
  * Alg. 4 reconstructs a long acquisition one mini-batch of consecutive frames
  * at a time.  The first mini-batch (alpha_1 frames) is an ordinary solve:

@@ -255,6 +255,7 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
     c->n_used = meta[MT_NUSED];
     c->n_lines = meta[MT_NLINES];
+    c->m_max = meta[MT_MMAX];
     c->total = (int64_t)c->n_lines * c->nx;
     if (c->total == 0 || c->n_used == 0) {
         set_err(c, "no sampled k-space");
@@ -530,6 +531,67 @@ extern "C" lrccs_status lrccs_track_minibatch(lrccs_ctx *c, const void *d_y, con
     return LRCCS_OK;
 }
 
+// ---------------------------------------------------------------- mean step (Alg. 1 steps 1 and 2a)
+
+// CG on A^H A z = A^H y at rank 1 (the context's r is set to 1 by the caller).
+static lrccs_status mean_cg(lrccs_ctx *c, const void *d_y, double tol, int max_iter, void *d_zbar, void *d_ytil,
+                           int32_t *out_iters) {
+    double *cg = (double *)c->d_tot;   // {gamma, alpha, stop}
+    double h[3];
+    CK(launch_cg_init(c, cg));
+    CK(cudaMemcpyAsync(h, cg, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double norms0 = sqrt(h[0]);
+    double gamma = h[0];
+    int it = 0;
+    while (it < max_iter && norms0 > 0.0 && sqrt(gamma) > tol * norms0) {
+        CK(launch_normal_op(c));
+        CK(launch_cg_step(c, cg));
+        CK(cudaMemcpyAsync(h, cg, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (h[2] != 0.0) break;   // <p, A^H A p> <= 0: nothing left to reduce
+        ++it;
+        gamma = h[0];
+    }
+    const size_t zb = (size_t)c->n * sizeof(float2);
+    CK(cudaMemcpyAsync(d_zbar, c->d_Uprev, zb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_ytil) {
+        CK(cudaMemcpyAsync(c->d_U, c->d_Uprev, zb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(launch_fwd_only(c));
+        CK(launch_mean_resid(c, (const float2 *)d_y, (float2 *)d_ytil, c->m_max / c->nx));
+    }
+    lrccs_status s = sync_status(c);
+    if (out_iters) *out_iters = it;
+    return s;
+}
+
+extern "C" lrccs_status lrccs_mean_step(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr,
+                                        const uint8_t *d_mask, const void *d_smaps, double tol, int32_t max_iter,
+                                        void *d_zbar, void *d_ytil, int32_t *out_iters) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps || !d_zbar || !(tol >= 0.0) || max_iter < 0 ||
+        max_iter > 10000) {
+        set_err(c, "lrccs_mean_step: null pointer, tol < 0 or max_iter outside [0, 10000]");
+        return LRCCS_E_INVALID;
+    }
+    if (d_ytil == d_y) {
+        set_err(c, "lrccs_mean_step: d_ytil must not alias d_y");
+        return LRCCS_E_INVALID;
+    }
+    // the CG vectors use the subspace buffers: the context holds no solve afterwards
+    c->initialized = 0;
+    c->has_u = 0;
+    c->need_h = 0;
+    c->t = 0;
+    lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, false);
+    if (s != LRCCS_OK) return s;
+    const int r_save = c->r;
+    c->r = 1;
+    s = mean_cg(c, d_y, tol, max_iter, d_zbar, d_ytil, out_iters);
+    c->r = r_save;
+    return s;
+}
+
 // State buffer: this header, then U (n x r complex64).
 struct state_header {
     uint32_t magic, version;
@@ -676,7 +738,7 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
-    "k_images"};
+    "k_images", "k_cg_init", "k_cg_step", "k_mean_resid"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

@@ -38,7 +38,7 @@ enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_COUNT = 8 };
 enum {
     KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
     KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_ROW_GRAM, KID_SOLVE, KID_ROW_W, KID_ADJ_COLS,
-    KID_IMAGES, KID_COUNT
+    KID_IMAGES, KID_CG_INIT, KID_CG_STEP, KID_MEAN_RESID, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -85,6 +85,7 @@ struct lrccs_ctx {
     int gd_grid;       // blocks of the cooperative GD/QR kernel (all resident)
     int n_used;        // host copy of MT_NUSED
     int n_lines;       // host copy of MT_NLINES
+    int m_max;         // host copy of MT_MMAX (largest per-frame sample count per coil)
     int64_t total;     // fp[q] (samples per coil, all frames)
     int dev_smem_optin;
     std::string err;
@@ -141,6 +142,11 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode);      // F: GD step + CholeskyQR
 cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);
+cudaError_t launch_normal_op(lrccs_ctx *c);           // U+ <- A^H A U, rank 1, b_k = 1
+cudaError_t launch_fwd_only(lrccs_ctx *c);            // T <- F_y(d_j o U) on the sampled rows
+cudaError_t launch_cg_init(lrccs_ctx *c, double *cg);
+cudaError_t launch_cg_step(lrccs_ctx *c, double *cg);
+cudaError_t launch_mean_resid(lrccs_ctx *c, const float2 *d_y, float2 *d_ytil, int nl_max);
 int npairs_of(int r);
 
 // Bits of the device status word ctx->d_status.

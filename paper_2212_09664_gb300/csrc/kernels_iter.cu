@@ -378,88 +378,122 @@ typedef void (*row_w_t)(float2 *, const float2 *, const int32_t *, const int32_t
 static const row_gram_t kRowGram[RMAXC] = RANK_TABLE(k_row_gram);
 static const row_w_t kRowW[RMAXC] = RANK_TABLE(k_row_w);
 
-cudaError_t launch_iteration(lrccs_ctx *c) {
+// One launcher per iteration kernel, at the context's current rank c->r.
+static cudaError_t launch_fwd_cols(lrccs_ctx *c) {
     const int r = c->r, nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
-    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
-    // A
-    {
-        const int tx = fwd_tile_x(r, nx);
-        const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
-        dim3 grid(nx / tx, c->nc);
-        DISPATCH_P(c->py, {
-            prof_begin(c, KID_FWD_COLS);
-            k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_U, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
-                                                           c->d_twy, sy);
-            prof_end(c, KID_FWD_COLS);
-        });
-    }
-    // B
-    {
-        const size_t smem = (size_t)2 * nx * r * sizeof(float2);
-        const int cgr = adj_cluster(c->nc);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(c->n_used, cgr, 1);
-        cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = c->stream;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 1;
-        at[0].val.clusterDim.y = cgr;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        prof_begin(c, KID_ROW_GRAM);
-        const cudaError_t el = cudaLaunchKernelEx(&cfg, kRowGram[r - 1], (const float2 *)c->d_T,
-                                                  (const int32_t *)c->d_usedrows, c->d_P, ny, nx, c->nc);
-        prof_end(c, KID_ROW_GRAM);
-        if (el != cudaSuccess) return el;
-    }
-    // C
-    launch_solve(c);
-    // D
-    {
-        const size_t smem = ((size_t)2 * nx * r + (size_t)c->q * r) * sizeof(float2);
-        prof_begin(c, KID_ROW_W);
-        kRowW[r - 1]<<<dim3(c->n_used, adj_cluster(c->nc)), 256, smem, c->stream>>>(
-            c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny, nx, c->nc, c->q);
-        prof_end(c, KID_ROW_W);
-    }
-    // E: coil-summed inverse transform into the U+ buffer (free during iterations)
-    {
-        const size_t smem = ((size_t)4 * ny * r + 5 * (size_t)ny) * sizeof(float2);
-        const int cg = adj_cluster(c->nc);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(nx, cg, 1);
-        cfg.blockDim = dim3(256, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = c->stream;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 1;
-        at[0].val.clusterDim.y = cg;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        const bool small = ny * r <= 256 * 8;
-        cudaError_t el = cudaSuccess;
-        DISPATCH_P(c->py, {
-            prof_begin(c, KID_ADJ_COLS);
-            if (small)
-                el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 8>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
-                                        (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
-            else
-                el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 16>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
-                                        (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
-            prof_end(c, KID_ADJ_COLS);
-        });
-        if (el != cudaSuccess) return el;
-    }
+    const int tx = fwd_tile_x(r, nx);
+    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
+    dim3 grid(nx / tx, c->nc);
+    DISPATCH_P(c->py, {
+        prof_begin(c, KID_FWD_COLS);
+        k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_U, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
+                                                       c->d_twy, sy);
+        prof_end(c, KID_FWD_COLS);
+    });
+    return cudaSuccess;
+}
+
+static cudaError_t launch_row_gram(lrccs_ctx *c) {
+    const int r = c->r, nx = c->nx, ny = c->ny;
+    const size_t smem = (size_t)2 * nx * r * sizeof(float2);
+    const int cgr = adj_cluster(c->nc);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->n_used, cgr, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = cgr;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    prof_begin(c, KID_ROW_GRAM);
+    const cudaError_t el = cudaLaunchKernelEx(&cfg, kRowGram[r - 1], (const float2 *)c->d_T,
+                                              (const int32_t *)c->d_usedrows, c->d_P, ny, nx, c->nc);
+    prof_end(c, KID_ROW_GRAM);
+    return el;
+}
+
+static void launch_row_w(lrccs_ctx *c) {
+    const int r = c->r, nx = c->nx, ny = c->ny;
+    const size_t smem = ((size_t)2 * nx * r + (size_t)c->q * r) * sizeof(float2);
+    prof_begin(c, KID_ROW_W);
+    kRowW[r - 1]<<<dim3(c->n_used, adj_cluster(c->nc)), 256, smem, c->stream>>>(
+        c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny, nx, c->nc, c->q);
+    prof_end(c, KID_ROW_W);
+}
+
+// coil-summed inverse transform into the U+ buffer (free during iterations)
+static cudaError_t launch_adj_cols(lrccs_ctx *c) {
+    const int r = c->r, nx = c->nx, ny = c->ny;
+    const float sy = (float)(1.0 / sqrt((double)ny));
+    const size_t smem = ((size_t)4 * ny * r + 5 * (size_t)ny) * sizeof(float2);
+    const int cg = adj_cluster(c->nc);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nx, cg, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = cg;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const bool small = ny * r <= 256 * 8;
+    cudaError_t el = cudaSuccess;
+    DISPATCH_P(c->py, {
+        prof_begin(c, KID_ADJ_COLS);
+        if (small)
+            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 8>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+                                    (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
+        else
+            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 16>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+                                    (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
+        prof_end(c, KID_ADJ_COLS);
+    });
+    return el;
+}
+
+cudaError_t launch_iteration(lrccs_ctx *c) {
+    if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    cudaError_t el = launch_fwd_cols(c);   // A
+    if (el != cudaSuccess) return el;
+    el = launch_row_gram(c);               // B
+    if (el != cudaSuccess) return el;
+    launch_solve(c);                       // C
+    launch_row_w(c);                       // D
+    el = launch_adj_cols(c);               // E
+    if (el != cudaSuccess) return el;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // F: gradient, GD step and CholeskyQR2 (one cooperative launch)
     return launch_gdqr(c, 1);
+}
+
+// The normal operator of the stacked A = [A_1; ...; A_q] with B = 1 (q x 1):
+// d_Up <- sum_j conj(d_j) o F^H[c o F(d_j o u)], u = d_U (n x 1), c_i the
+// number of frames that sample k-space row i (W_i of the gradient with r = 1).
+cudaError_t launch_normal_op(lrccs_ctx *c) {
+    if (c->r != 1) return cudaErrorInvalidValue;
+    cudaError_t el = launch_fwd_cols(c);
+    if (el != cudaSuccess) return el;
+    launch_row_w(c);
+    el = launch_adj_cols(c);
+    if (el != cudaSuccess) return el;
+    return cudaGetLastError();
+}
+
+// d_T <- F_y(d_j o U) on the sampled rows (the first step of an iteration).
+cudaError_t launch_fwd_only(lrccs_ctx *c) {
+    if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    cudaError_t el = launch_fwd_cols(c);
+    if (el != cudaSuccess) return el;
+    return cudaGetLastError();
 }
 
 __global__ void k_images(const float2 *__restrict__ Uprev, const float2 *__restrict__ B, float2 *__restrict__ X,

@@ -61,6 +61,7 @@ _sig = {
     "lrccs_profile_reset": (_st, [_vp]),
     "lrccs_trunc_threshold_noalloc": (_st, [_vp, C.c_int64, C.c_double, _vp, _vp]),
     "lrccs_set_subspace": (_st, [_vp, _vp, C.c_int32, C.c_double]),
+    "lrccs_mean_step": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_int32, _vp, _vp, C.POINTER(C.c_int32)]),
     "lrccs_track_minibatch": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.POINTER(IterInfo)]),
     "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
@@ -175,6 +176,13 @@ def lrccs_trunc_threshold_noalloc(y, count, trunc_factor, gamma_out, stream=None
     _check(None, _lib.lrccs_trunc_threshold_noalloc(_ptr(y), int(count), float(trunc_factor), _ptr(gamma_out), s))
 
 
+def lrccs_mean_step(ctx, y, frame_ptr, mask, smaps, zbar, ytil=None, tol: float = 1e-3, max_iter: int = 10) -> int:
+    it = C.c_int32(0)
+    _check(ctx, _lib.lrccs_mean_step(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps), float(tol),
+                                     int(max_iter), _ptr(zbar), _ptr(ytil), C.byref(it)))
+    return it.value
+
+
 def lrccs_set_subspace(ctx, U, rank: int, eta: float = 0.0):
     _check(ctx, _lib.lrccs_set_subspace(ctx, _ptr(U), int(rank), float(eta)))
 
@@ -240,6 +248,14 @@ class Solver:
 
     def iterate(self, n_iter, info=False):
         return lrccs_iterate(self.ctx, n_iter, info)
+
+    def mean_step(self, y, frame_ptr, mask, smaps, tol=1e-3, max_iter=10):
+        """Alg. 1 steps 1 and 2a: returns (zbar (n,), y~ (like y), CG iterations run)."""
+        t = self._torch
+        zbar = t.empty((self.n,), dtype=t.complex64, device=y.device)
+        ytil = t.empty_like(y)
+        it = lrccs_mean_step(self.ctx, y, frame_ptr, mask, smaps, zbar, ytil, tol, max_iter)
+        return zbar, ytil, it
 
     def set_subspace(self, U, eta=0.0):
         """U_0 <- U (n x r) for the next tracking call or iteration; eta > 0 fixes the step size."""
