@@ -12,9 +12,9 @@ Metric: frame-iterations/s = q * 50 / (step time), whole job over all ranks.
 After the timed solves (N = 1 only) a serving leg runs mini-batch subspace
 tracking (Alg. 4) as a real-time request loop over 8 acquisitions and reports
 the p50/p99 arrival-to-reconstruction latency of its mini-batches
-(--no-serving skips it), and cuFFT / cuBLAS versions of the transform and
-gradient-step products are timed beside the fused kernels (--no-comparators
-skips them).
+(--no-serving skips it).  cuFFT / cuBLAS versions of the transform and
+gradient-step products are timed beside the fused kernels, and Alg. 1's mean
+step (lrccs_mean_step) is timed on the workload (--no-comparators skips both).
 
 --impl reference times the FP64 CPU oracle (the only reference this work has)
 on a bounded sample of the same workload and extrapolates to a 50-iteration
@@ -406,6 +406,37 @@ def library_comparators(p, dev, used_rows, stats):
     return out
 
 
+def mean_step_leg(p, dev, stream, reps=10):
+    """Alg. 1 steps 1 and 2a on the workload through lrccs_mean_step (CGLS with the
+    paper's tolerance 1e-3 and at most 10 iterations, then y~ = y - A zbar): time
+    per call with CUDA events on the library stream, inputs resident.  The call
+    waits for the stopping test after every CG step, so the time includes those
+    host round trips."""
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs
+
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    with torch.cuda.stream(stream):
+        y, fp, mask, sm = (torch.from_numpy(a).to(dev) for a in (p.y, p.frame_ptr, p.mask, p.smaps))
+        zbar = torch.empty((p.n,), dtype=torch.complex64, device=dev)
+        ytil = torch.empty_like(y)
+    it = 0
+    for _ in range(2):
+        it = lrccs.lrccs_mean_step(s.ctx, y, fp, mask, sm, zbar, ytil)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        it = lrccs.lrccs_mean_step(s.ctx, y, fp, mask, sm, zbar, ytil)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    s.close()
+    return dict(ms_per_call=ms, cg_iterations=it, calls=reps,
+                includes="mask compaction, Z passes for A^H y, CG steps (normal operator = rank-1 iteration "
+                         "transforms), residual pass")
+
+
 def serving_parity(part, U_prev, eta, X_gpu):
     """NRMSE of one tracked mini-batch's images against the FP64 oracle run from the
     same warm start U^(j-1) and step size (part of the CPU-baseline leg)."""
@@ -576,6 +607,11 @@ def main():
             line["comparators"] = library_comparators(p, dev, used, stats)
         except Exception as e:
             line["comparators"] = dict(error="%s: %s" % (type(e).__name__, e))
+    if ws == 1 and not args.no_comparators:
+        try:
+            line["mean_step"] = mean_step_leg(p, dev, stream)
+        except Exception as e:
+            line["mean_step"] = dict(error="%s: %s" % (type(e).__name__, e))
     sv_check = None
     if ws == 1 and not args.no_serving:
         try:
