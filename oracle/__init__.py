@@ -220,38 +220,22 @@ class Operator:
         return out
 
 
-def mean_step(op, y, tol=1e-3, maxit=10):
-    """Alg. 1 step 1: zbar = argmin_z sum_k ||y_k - A_k z||^2 by CGLS (conjugate
-    gradients on the normal equations A^H A z = A^H y of the stacked operator
-    A = [A_1; ...; A_q], started at z = 0), stopped after maxit iterations or
-    once ||A^H r_t|| <= tol ||A^H y||; then the residual measurements
-    y~_k = y_k - A_k zbar (Alg. 1 step 2a).  Returns dict(zbar, ytil, iters,
-    normal_res: ||A^H r_t|| for t = 0..iters)."""
-    y = _c128(y)
-    q = op.q
-
-    def A(z):
-        return np.concatenate([op.forward(k, z) for k in range(q)])
-
-    def AH(v):
-        out = np.zeros(op.n, dtype=np.complex128)
-        for k in range(q):
-            a = op.yoff(k)
-            out += op.adjoint(k, v[a: a + op.rows(k)])
-        return out
-
-    z = np.zeros(op.n, dtype=np.complex128)
-    res = y.copy()                      # r_0 = y - A z_0
+def _cgls(A, AH, b, n, tol, maxit):
+    """CGLS (conjugate gradients on A^H A x = A^H b) from x = 0: at most maxit
+    iterations, stopping once ||A^H r_t|| <= tol ||A^H b||.  Returns
+    (x, iterations, [||A^H r_t|| for t = 0..iterations])."""
+    x = np.zeros(n, dtype=np.complex128)
+    res = b.copy()                      # r_0 = b - A x_0
     s = AH(res)                         # normal residual A^H r
     p = s.copy()
     gamma = np.vdot(s, s).real
     norms0 = math.sqrt(gamma)
     hist = [norms0]
     t = 0
-    while t < maxit and hist[-1] > tol * norms0 and norms0 > 0:
+    while t < maxit and hist[-1] > tol * norms0 and gamma > 0:
         w = A(p)
         alpha = gamma / np.vdot(w, w).real
-        z = z + alpha * p
+        x = x + alpha * p
         res = res - alpha * w
         s = AH(res)
         gamma_new = np.vdot(s, s).real
@@ -259,7 +243,81 @@ def mean_step(op, y, tol=1e-3, maxit=10):
         gamma = gamma_new
         hist.append(math.sqrt(gamma))
         t += 1
-    return dict(zbar=z, ytil=y - A(z), iters=t, normal_res=np.array(hist))
+    return x, t, np.array(hist)
+
+
+def _frame(op, v, k):
+    a = op.yoff(k)
+    return v[a: a + op.rows(k)]
+
+
+def _A_all(op, E):
+    """[A_k e_k]_k concatenated in the layout of y (E: n x q)."""
+    return np.concatenate([op.forward(k, E[:, k]) for k in range(op.q)])
+
+
+def _AH_all(op, v):
+    """n x q matrix with column k = A_k^H v_k."""
+    return np.stack([op.adjoint(k, _frame(op, v, k)) for k in range(op.q)], 1)
+
+
+def mean_step(op, y, tol=1e-3, maxit=10):
+    """Alg. 1 step 1: zbar = argmin_z sum_k ||y_k - A_k z||^2 by CGLS on the
+    stacked operator A = [A_1; ...; A_q] from z = 0, stopped after maxit
+    iterations or once ||A^H r_t|| <= tol ||A^H y||; then the residual
+    measurements y~_k = y_k - A_k zbar (Alg. 1 step 2a).  Returns dict(zbar,
+    ytil, iters, normal_res: ||A^H r_t|| for t = 0..iters)."""
+    y = _c128(y)
+
+    def A(z):
+        return np.concatenate([op.forward(k, z) for k in range(op.q)])
+
+    def AH(v):
+        return _AH_all(op, v).sum(1)
+
+    z, t, hist = _cgls(A, AH, y, op.n, tol, maxit)
+    return dict(zbar=z, ytil=y - A(z), iters=t, normal_res=hist)
+
+
+def mec1(op, ytt, iters=3):
+    """Alg. 3, unstructured MEC (altGDmin-MRI1): for every frame, `iters` CGLS
+    iterations from e = 0 on min_e ||ytt_k - A_k e||^2 (the paper's tolerance
+    1e-36 never stops them early).  ytt: residual measurements
+    y_k - A_k zbar - A_k x_k in the layout of y.  Returns E (n x q)."""
+    ytt = _c128(ytt)
+    E = np.zeros((op.n, op.q), dtype=np.complex128)
+    for k in range(op.q):
+        E[:, k] = _cgls(lambda e: op.forward(k, e), lambda v: op.adjoint(k, v), _frame(op, ytt, k), op.n,
+                        0.0, iters)[0]
+    return E
+
+
+def soft_threshold(M, omega):
+    """Complex soft threshold: M_i (|M_i| - omega)/|M_i| where |M_i| > omega, else 0."""
+    a = np.abs(M)
+    return np.where(a > omega, M * (1.0 - omega / np.where(a > 0, a, 1.0)), 0.0)
+
+
+def mec2(op, ytt, max_iter=10, rel_change=0.0025, frac=0.001):
+    """Alg. 3, sparse MEC (altGDmin-MRI2): ISTA for E with a sparse temporal
+    Fourier transform.  From E_0 = 0, step tau computes
+        M_tau = F_t(E_tau + A^H(ytt - A(E_tau))),   F_t: DFT along the frames,
+    sets omega = frac max|M_0| at tau = 0, and E_{tau+1} = F_t^{-1}(SThr_omega(M_tau));
+    it stops after max_iter updates or once ||M_tau - M_{tau-1}||_F <
+    rel_change ||M_{tau-1}||_F.  Returns dict(E (n x q), iters, omega)."""
+    ytt = _c128(ytt)
+    E = np.zeros((op.n, op.q), dtype=np.complex128)
+    M_prev, omega, tau = None, None, 0
+    while tau < max_iter:
+        M = np.fft.fft(E + _AH_all(op, ytt - _A_all(op, E)), axis=1, norm="ortho")
+        if omega is None:
+            omega = frac * np.abs(M).max()
+        if M_prev is not None and np.linalg.norm(M - M_prev) < rel_change * np.linalg.norm(M_prev):
+            break
+        E = np.fft.ifft(soft_threshold(M, omega), axis=1, norm="ortho")
+        M_prev = M
+        tau += 1
+    return dict(E=E, iters=tau, omega=omega)
 
 
 def track_minibatches(batches, rank, t_first=70, t_next=5, params: Params = None, reset_eta=False,
