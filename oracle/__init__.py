@@ -320,6 +320,19 @@ def mec2(op, ytt, max_iter=10, rel_change=0.0025, frac=0.001):
     return dict(E=E, iters=tau, omega=omega)
 
 
+def online_frames(op, y, zbar, U, mec_iters=3):
+    """Alg. 5 step 2 (online subspace tracking) for the frames of `op`, all after
+    the first mini-batch: with that mini-batch's mean zbar and subspace U held
+    fixed, every frame gets y~_k = y_k - A_k zbar, b_k = (A_k U)^+ y~_k (the
+    B-step), e_k from `mec_iters` CGLS steps on y~_k - A_k U b_k (MEC-1), and
+    x_k = zbar + U b_k + e_k.  Returns dict(X (n x q), B (r x q), E (n x q))."""
+    y, zbar, U = _c128(y), _c128(zbar), _c128(U)
+    ytil = y - _A_all(op, np.repeat(zbar[:, None], op.q, 1))
+    B = op.bstep(ytil, U)
+    E = mec1(op, ytil - _A_all(op, U @ B), mec_iters)
+    return dict(X=zbar[:, None] + U @ B + E, B=B, E=E)
+
+
 def track_minibatches(batches, rank, t_first=70, t_next=5, params: Params = None, reset_eta=False,
                       U_start=None, eta_start=0.0):
     """Mini-batch subspace tracking (Alg. 4) over `batches`, a list of
