@@ -189,9 +189,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(p, y_ref_X2):
-    """Oracle timing on a bounded sample (init + 2 iterations), plus the
-    NRMSE of the GPU's X_2 against the oracle's X_2 on the same inputs."""
+def cpu_baseline(p, X_final):
+    """The oracle's whole solve of the workload (init + T_ITER iterations, about
+    40 s on 16 host cores), timed, and the NRMSE of the GPU's final iterate
+    X_T = U_{T-1} B_T against the oracle's X_T on the same inputs: the gate the
+    metric is defined by (NRMSE <= 1e-3)."""
     import numpy as np
 
     import oracle
@@ -200,16 +202,14 @@ def cpu_baseline(p, y_ref_X2):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     t0 = time.perf_counter()
     ini = op.init(p.y, rank=p.rank)
+    it = op.iterate(p.y, ini["U0"], T_ITER)
     t1 = time.perf_counter()
-    it = op.iterate(p.y, ini["U0"], 2, history=True)
-    t2 = time.perf_counter()
-    t_iter = (t2 - t1) / 2
-    value = p.q * T_ITER / ((t1 - t0) + T_ITER * t_iter)
-    Xr = it["X"][1]
-    nrmse = float(np.linalg.norm(y_ref_X2 - Xr) / np.linalg.norm(Xr))
+    value = p.q * T_ITER / (t1 - t0)
+    Xr = it["Uprev"] @ it["B"]
+    nrmse = float(np.linalg.norm(X_final - Xr) / np.linalg.norm(Xr))
     return dict(value=value, unit=UNIT, cores=cores, kind="oracle",
-                sample="oracle init + 2 GDmin iterations of %s (%.1f s); the %d-iteration solve is "
-                       "extrapolated as t_init + %d t_iter" % (WORKLOAD, t2 - t0, T_ITER, T_ITER)), nrmse
+                sample="oracle init + %d GDmin iterations of %s: one whole solve (%.1f s), not extrapolated"
+                       % (T_ITER, WORKLOAD, t1 - t0)), nrmse
 
 
 # Serving form of Alg. 4: mini-batch subspace tracking as a request loop.
@@ -621,14 +621,15 @@ def main():
         except Exception as e:        # the solve's line is still printed; the failure is reported in it
             line["serving"] = dict(error="%s: %s" % (type(e).__name__, e))
     if ws == 1 and not args.no_cpu_baseline:
-        # X_2 of the GPU for the parity figure reported beside the oracle timing
-        lrccs.lrccs_init(s.ctx, y, fp, mask, sm)
-        lrccs.lrccs_iterate(s.ctx, 2)
-        lrccs.lrccs_get_factors(s.ctx, U, B)
-        X2 = (U @ B.T).cpu().numpy().astype(np.complex128)
-        cb, nr = cpu_baseline(p, X2)
+        # the final iterate of the timed solve (init + T_ITER graph-replayed
+        # iterations, the same calls as a timed step) against the FP64 oracle
+        step()
+        stream.synchronize()
+        XT = (U @ B.T).cpu().numpy().astype(np.complex128)
+        cb, nr = cpu_baseline(p, XT)
         line["cpu_baseline"] = cb
-        line["nrmse_x2_vs_fp64"] = nr
+        line["nrmse_final_vs_fp64"] = nr
+        line["valid_at_nrmse_1e-3"] = bool(nr <= 1e-3)
         if sv_check is not None:
             line["serving"]["nrmse_last_minibatch_vs_fp64"] = serving_parity(*sv_check)
     s.close()

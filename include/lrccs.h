@@ -33,7 +33,7 @@
  *                 lrccs_iterate when info is requested).
  *
  * Scope of this build: images with ny, nx multiples of 32 in [32, 256];
- * rank r <= 16; q <= 256 frames; C <= 64 coils; every frame's mask must be a
+ * rank r <= 16; q <= 128 frames; C <= 64 coils; every frame's mask must be a
  * union of full phase-encode lines (1D Cartesian sampling, Sec. V); other
  * masks return LRCCS_E_UNSUPPORTED.
  */
@@ -296,7 +296,10 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
  * which loads the library holds until the process exits.  The first call on a
  * device looks up that array's device address with the device current (a
  * cudaGetSymbolAddress), so make the first call on each device before any
- * stream capture.  Every call shares the array and clears its counter before
+ * stream capture.  The address is kept for the life of the process, so this
+ * entry point must not be used on a device after cudaDeviceReset (which
+ * reloads the library's device code at a new address).  Every call shares the
+ * array and clears its counter before
  * use; calls whose work overlaps on the GPU (different streams, or another
  * host thread) race on it and must be serialised by the caller.
  * Errors: LRCCS_E_INVALID for null pointers or count outside
@@ -304,6 +307,19 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
 #define LRCCS_NOALLOC_MAX_ENTRIES ((int64_t)268435456)
 lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor, double *d_gamma,
                                            void *cuda_stream);
+
+/* Test support for the bounded device waits (the paper has no counterpart).
+ * With enable != 0 the next directly launched GD/QR kernel of this context (an
+ * lrccs_iterate of one iteration, or one with exit_enabled or info) waits at
+ * each grid barrier for one arrival more than its grid can make and gives up
+ * after 2^16 polls instead of 2^24, so every barrier times out.  The kernel
+ * still runs to its end (its results are then meaningless), the device status
+ * word records the timeout and the next synchronising call returns
+ * LRCCS_E_TIMEOUT.  The setting applies to that one launch and is never
+ * captured into an iteration graph.  A later lrccs_init (or tracking call)
+ * resets the status and the subspace, after which the context works as before.
+ * Errors: LRCCS_E_INVALID (null ctx). */
+lrccs_status lrccs_test_wait_timeout(lrccs_ctx *ctx, int32_t enable);
 
 /* Wait for the context's stream and return any device-side failure. */
 lrccs_status lrccs_synchronize(lrccs_ctx *ctx);

@@ -203,6 +203,10 @@ extern "C" void lrccs_destroy(lrccs_ctx *c) {
 }
 
 static lrccs_status status_to_code(lrccs_ctx *c, unsigned st) {
+    if (st & ST_TIMEOUT) {   // first: a barrier that gave up explains any other flag
+        set_err(c, "a bounded device wait timed out");
+        return LRCCS_E_TIMEOUT;
+    }
     if (st & ST_PARTIAL_ROWS) {
         set_err(c, "mask has partially sampled rows; this build supports unions of full phase-encode lines only");
         return LRCCS_E_UNSUPPORTED;
@@ -222,10 +226,6 @@ static lrccs_status status_to_code(lrccs_ctx *c, unsigned st) {
     if (st & ST_NOT_SPD_QR) {
         set_err(c, "U + eta grad lost rank (CholeskyQR failed)");
         return LRCCS_E_RANK_DEFICIENT;
-    }
-    if (st & ST_TIMEOUT) {
-        set_err(c, "a bounded device wait timed out");
-        return LRCCS_E_TIMEOUT;
     }
     return LRCCS_OK;
 }
@@ -829,6 +829,12 @@ extern "C" lrccs_status lrccs_profile_reset(lrccs_ctx *c) {
         c->prof_ms[k] = 0.0;
     }
     return s;
+}
+
+extern "C" lrccs_status lrccs_test_wait_timeout(lrccs_ctx *c, int32_t enable) {
+    if (!c) return LRCCS_E_INVALID;
+    c->test_timeout = enable ? 1 : 0;
+    return LRCCS_OK;
 }
 
 extern "C" lrccs_status lrccs_synchronize(lrccs_ctx *c) {

@@ -88,6 +88,7 @@ struct lrccs_ctx {
     int m_max;         // host copy of MT_MMAX (largest per-frame sample count per coil)
     int64_t total;     // fp[q] (samples per coil, all frames)
     int dev_smem_optin;
+    int test_timeout;  // lrccs_test_wait_timeout: the next direct k_gdqr launch waits for an unreachable barrier
     std::string err;
 
     // geometry / sampling

@@ -49,23 +49,28 @@ struct GdArgs {
     unsigned int *status;
     int n, r, q, zs, chunk, resident, mode;
     double eta_c;
+    unsigned int spin_limit;   // polls before a grid barrier gives up (2^24 normally)
+    unsigned int bar_skew;     // extra arrivals a barrier waits for (0; 1 only for the timeout test)
 };
 
 // ---------------------------------------------------------------- grid-wide steps
 
 // Barrier number k (1, 2, ...) of this launch: wait until every block has
-// arrived k times.  Bounded: gives up after ~1 s and raises ST_TIMEOUT.
-static __device__ void grid_sync(unsigned int *bar, unsigned int k, unsigned int *status) {
+// arrived k times (plus `skew` arrivals, which only the timeout test sets and
+// the grid can never make).  Bounded: gives up after `limit` polls (2^24, about
+// a second) and raises ST_TIMEOUT; the kernel then runs on to its end.
+static __device__ void grid_sync(unsigned int *bar, unsigned int k, unsigned int *status, unsigned int limit,
+                                 unsigned int skew) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int target = k * gridDim.x;
+        const unsigned int target = k * gridDim.x + skew;
         __threadfence();
         atomicAdd(bar, 1u);
         unsigned int v = 0, spins = 0;
         while (true) {
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(bar) : "memory");
             if (v >= target) break;
-            if (++spins > (1u << 24)) {
+            if (++spins > limit) {
                 atomicOr(status, (unsigned)ST_TIMEOUT);
                 break;
             }
@@ -429,9 +434,9 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         if (x > y) return -1;
         return (kind == 2 && iter ? np + rr : 0) + pair_index(x, y, r);
     });
-    grid_sync(a.bar, 1, a.status);
+    grid_sync(a.bar, 1, a.status, a.spin_limit, a.bar_skew);
     grid_reduce(a.part, len1, a.tot);
-    grid_sync(a.bar, 2, a.status);
+    grid_sync(a.bar, 2, a.status, a.spin_limit, a.bar_skew);
     for (int e = t; e < len1; e += NTG) {
         const double2 v = __ldcg(a.tot + e);
         s_tot[e] = make_float2((float)v.x, (float)v.y);
@@ -591,7 +596,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             }
         }
     }
-    grid_sync(a.bar, 3, a.status);
+    grid_sync(a.bar, 3, a.status, a.spin_limit, a.bar_skew);
     grid_reduce(a.part, len2, a.tot);
     // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2, and
     // the barrier counters back to zero (every block is past its last barrier)
@@ -679,6 +684,13 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.resident = chunk >= per ? 1 : 0;
     a.mode = mode;
     a.eta_c = c->prm.eta_c;
+    a.spin_limit = 1u << 24;
+    a.bar_skew = 0;
+    if (c->test_timeout && !c->capturing) {   // lrccs_test_wait_timeout: this launch only
+        a.spin_limit = 1u << 16;
+        a.bar_skew = 1;
+        c->test_timeout = 0;
+    }
     void *args[] = {&a};
     const size_t smem = (size_t)chunk * bpp;
     prof_begin(c, KID_GDQR);

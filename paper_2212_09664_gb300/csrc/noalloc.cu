@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_energy_noalloc(const float2 *__r
     }
 }
 
-// Device address of g_na_scratch, resolved once per device.
+// Device address of g_na_scratch, resolved once per device and kept for the
+// life of the process (a cudaDeviceReset would move it; the header forbids
+// calls after one).
 static std::mutex g_na_mutex;
 static na_scratch *g_na_addr[256];
 

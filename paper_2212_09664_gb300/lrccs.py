@@ -65,6 +65,7 @@ _sig = {
     "lrccs_track_minibatch": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.POINTER(IterInfo)]),
     "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
+    "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
     "lrccs_destroy": (None, [_vp]),
     "lrccs_last_error": (C.c_char_p, [_vp]),
     "lrccs_status_string": (C.c_char_p, [_st]),
@@ -172,8 +173,24 @@ def lrccs_trunc_threshold_noalloc(y, count, trunc_factor, gamma_out, stream=None
     tensor), computed without any device allocation (for callers that reserve
     their device memory up front and may not allocate).  The scratch is a fixed
     array inside the library shared by all calls: do not overlap calls on the GPU."""
+    import torch
+
+    # The C side can only bound count by the scratch size; everything that
+    # keeps the kernel inside y's allocation is checked here, before any launch.
+    if y.dtype != torch.complex64:
+        raise ValueError("y must be complex64, got %s" % y.dtype)
+    if gamma_out.dtype != torch.float64 or gamma_out.numel() < 1:
+        raise ValueError("gamma_out must be a float64 tensor with at least one element")
+    count = int(count)
+    if not 1 <= count <= y.numel():
+        raise ValueError("count = %d outside [1, y.numel() = %d]" % (count, y.numel()))
+    if not (y.is_cuda and gamma_out.is_cuda):
+        raise ValueError("y and gamma_out must be CUDA tensors")
+    cur = torch.cuda.current_device()
+    if y.device.index != cur or gamma_out.device.index != cur:
+        raise ValueError("y and gamma_out must be on the current device (cuda:%d)" % cur)
     s = None if stream is None else _vp(stream.cuda_stream)
-    _check(None, _lib.lrccs_trunc_threshold_noalloc(_ptr(y), int(count), float(trunc_factor), _ptr(gamma_out), s))
+    _check(None, _lib.lrccs_trunc_threshold_noalloc(_ptr(y), count, float(trunc_factor), _ptr(gamma_out), s))
 
 
 def lrccs_mean_step(ctx, y, frame_ptr, mask, smaps, zbar, ytil=None, tol: float = 1e-3, max_iter: int = 10) -> int:
@@ -209,6 +226,10 @@ def lrccs_get_state(ctx) -> bytes:
 
 def lrccs_set_state(ctx, state: bytes):
     _check(ctx, _lib.lrccs_set_state(ctx, state, len(state)))
+
+
+def lrccs_test_wait_timeout(ctx, enable: bool = True):
+    _check(ctx, _lib.lrccs_test_wait_timeout(ctx, 1 if enable else 0))
 
 
 def lrccs_last_error(ctx=None) -> str:

@@ -97,3 +97,27 @@ def test_null_context_is_rejected_before_any_device_work(lib):
     assert L.lrccs_track_minibatch(None, None, None, None, None, 5, 0, None, None) == lrccs.E_INVALID
     assert L.lrccs_get_state(None, None, C.byref(n)) == lrccs.E_INVALID
     assert L.lrccs_set_state(None, b"x" * 64, 64) == lrccs.E_INVALID
+
+
+def test_noalloc_wrapper_validates_before_any_launch(lib):
+    """The allocation-free threshold's binding refuses, before calling the
+    library, every argument that would let the kernel read outside y: a wrong
+    dtype, a count above y.numel(), a gamma_out that is not float64, and
+    tensors that are not on the current CUDA device."""
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs
+
+    y = torch.zeros(8, dtype=torch.complex64)
+    g = torch.zeros(1, dtype=torch.float64)
+    bad = [
+        (torch.zeros(8, dtype=torch.complex128), 8, g),      # not complex64
+        (y, 9, g),                                            # count above y.numel()
+        (y, 0, g),                                            # empty count
+        (y, 8, torch.zeros(1, dtype=torch.float32)),          # gamma_out not float64
+        (y, 8, torch.zeros(0, dtype=torch.float64)),          # no room for gamma
+        (y, 8, g),                                            # host tensors, not CUDA
+    ]
+    for yy, cnt, gg in bad:
+        with pytest.raises(ValueError):
+            lrccs.lrccs_trunc_threshold_noalloc(yy, cnt, 36.0, gg)

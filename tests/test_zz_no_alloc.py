@@ -48,9 +48,13 @@ def test_noalloc_threshold_matches_context_path_twice(spec):
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
+    """The C entry point refuses a count above its scratch capacity before any
+    launch (called directly: the Python wrapper would already refuse a count
+    above y.numel())."""
     y = torch.zeros(4, dtype=torch.complex64, device=DEV)
     out = torch.zeros(1, dtype=torch.float64, device=DEV)
-    with pytest.raises(lrccs.LrccsError) as ei:
-        lrccs.lrccs_trunc_threshold_noalloc(y, (1 << 28) + 1, 36.0, out)
-    assert ei.value.status == lrccs.E_INVALID
-    assert "outside" in str(ei.value)
+    st = lrccs._lib.lrccs_trunc_threshold_noalloc(y.data_ptr(), (1 << 28) + 1, 36.0, out.data_ptr(), None)
+    assert st == lrccs.E_INVALID
+    assert "outside" in lrccs.lrccs_last_error(None)
+    with pytest.raises(ValueError):
+        lrccs.lrccs_trunc_threshold_noalloc(y, 5, 36.0, out)
