@@ -26,6 +26,7 @@ void set_err(lrccs_ctx *c, const char *fmt, ...) {
 cudaError_t configure_kernels_init(int max_smem);
 cudaError_t configure_kernels_iter(int max_smem);
 cudaError_t configure_kernels_gd(int max_smem);
+cudaError_t configure_kernels_general(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -67,7 +68,9 @@ static void free_all(lrccs_ctx *c) {
     void *ptrs[] = {c->d_twy, c->d_twx, c->d_smaps, c->d_rowcnt, c->d_rowidx, c->d_framerows, c->d_lineptr,
                     c->d_rfptr, c->d_rflist, c->d_usedrows, c->d_rowused, c->d_idx, c->d_meta, c->d_status,
                     c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
-                    c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot};
+                    c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot, c->d_framek,
+                    c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
+                    c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -152,7 +155,9 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
               dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)ny * npm) &&
               dalloc(c, &c->d_gpart, gcap) && dalloc(c, &c->d_tot, gd_len) &&
               dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)2 * q * q) &&
-              dalloc(c, &c->d_V, (size_t)q * q);
+              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_framek, (size_t)q * ny) &&
+              dalloc(c, &c->d_mks, (size_t)q) && dalloc(c, &c->d_fpk, (size_t)q + 1) &&
+              dalloc(c, &c->d_rowoff, (size_t)q * ny);
     if (!ok) {
         g_create_err = c->err;
         free_all(c);
@@ -166,6 +171,7 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     cudaError_t e = configure_kernels_init(optin);
     if (e == cudaSuccess) e = configure_kernels_iter(optin);
     if (e == cudaSuccess) e = configure_kernels_gd(optin);
+    if (e == cudaSuccess) e = configure_kernels_general(optin);
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
@@ -207,10 +213,6 @@ static lrccs_status status_to_code(lrccs_ctx *c, unsigned st) {
         set_err(c, "a bounded device wait timed out");
         return LRCCS_E_TIMEOUT;
     }
-    if (st & ST_PARTIAL_ROWS) {
-        set_err(c, "mask has partially sampled rows; this build supports unions of full phase-encode lines only");
-        return LRCCS_E_UNSUPPORTED;
-    }
     if (st & ST_FRAMEPTR_MISMATCH) {
         set_err(c, "frame_ptr does not match the per-frame sample counts of the mask");
         return LRCCS_E_INVALID;
@@ -237,10 +239,27 @@ static lrccs_status sync_status(lrccs_ctx *c) {
     return status_to_code(c, st);
 }
 
+// Buffers of the general-mask path (allocated the first time a context sees
+// a mask with partly sampled rows).
+static lrccs_status ensure_general_buffers(lrccs_ctx *c) {
+    if (c->gen_cap_q) return LRCCS_OK;
+    const size_t n = (size_t)c->n, q = (size_t)c->q, ny = (size_t)c->ny;
+    const size_t npm = (size_t)c->rmax * (c->rmax + 1) / 2;
+    const bool ok = dalloc(c, &c->d_ucnt, n) && dalloc(c, &c->d_uloc, n) && dalloc(c, &c->d_floc, n) &&
+                    dalloc(c, &c->d_urow, 2 * ny) && dalloc(c, &c->d_uptr, ny + 1) &&
+                    dalloc(c, &c->d_ufrow, ny + 1) && dalloc(c, &c->d_upos, n) && dalloc(c, &c->d_uidx, n) &&
+                    dalloc(c, &c->d_ufptr, n + 1) && dalloc(c, &c->d_uflist, q * n) && dalloc(c, &c->d_fu, q * n) &&
+                    dalloc(c, &c->d_FU, (size_t)c->nc * n * c->rmax) && dalloc(c, &c->d_Pu, n * npm);
+    if (!ok) return LRCCS_E_NOMEM;
+    c->gen_cap_q = q;
+    return LRCCS_OK;
+}
+
 // Mask compaction, the sampled-row structure and Z = [A_k^H y_k] for the data
 // of one lrccs_init or tracking call; with_energy also forms gamma, which only
-// the spectral initialisation's truncation uses.  Waits once, for the
-// compaction's counts.
+// the spectral initialisation's truncation uses.  Waits for the compaction's
+// counts (twice for a general 2D mask: once for the row structure, once for
+// the union of the frames' samples).
 static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr, const uint8_t *d_mask,
                               const void *d_smaps, bool with_energy) {
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
@@ -256,12 +275,25 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     c->n_used = meta[MT_NUSED];
     c->n_lines = meta[MT_NLINES];
     c->m_max = meta[MT_MMAX];
-    c->total = (int64_t)c->n_lines * c->nx;
+    c->total = meta[MT_TOTAL];
+    c->general = meta[MT_GENERAL] ? 1 : 0;
+    c->n_u = 0;
     if (c->total == 0 || c->n_used == 0) {
         set_err(c, "no sampled k-space");
         return LRCCS_E_INVALID;
     }
-    const size_t need = (size_t)2 * c->nc * c->total;
+    if (c->general) {
+        s = ensure_general_buffers(c);
+        if (s != LRCCS_OK) return s;
+        CK(launch_compact_general(c, d_mask));
+        CK(cudaMemcpyAsync(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->n_u = meta[MT_NU];
+    } else {
+        CK(launch_fill_lines(c));
+    }
+    // init row pass: full rows (nx) for every (frame row, coil), plain and truncated
+    const size_t need = (size_t)2 * c->nc * c->n_lines * c->nx;
     if (need > c->T_cap) {
         cudaFree(c->d_T);
         c->d_T = nullptr;
@@ -347,7 +379,8 @@ static void drop_iter_graph(lrccs_ctx *c) {
 
 static bool graph_matches(const lrccs_ctx *c, int n_iter) {
     return c->iter_exec && c->iter_n == n_iter && c->iter_mask == c->prof_mask && c->iter_r == c->r &&
-           c->iter_nused == c->n_used && c->iter_T == c->d_T;
+           c->iter_nused == c->n_used && c->iter_T == c->d_T && c->iter_general == c->general &&
+           c->iter_nu == c->n_u;
 }
 
 static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
@@ -418,6 +451,8 @@ static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
     c->iter_r = c->r;
     c->iter_nused = c->n_used;
     c->iter_T = c->d_T;
+    c->iter_general = c->general;
+    c->iter_nu = c->n_u;
     return true;
 }
 
@@ -558,7 +593,8 @@ static lrccs_status mean_cg(lrccs_ctx *c, const void *d_y, double tol, int max_i
     if (d_ytil) {
         CK(cudaMemcpyAsync(c->d_U, c->d_Uprev, zb, cudaMemcpyDeviceToDevice, c->stream));
         CK(launch_fwd_only(c));
-        CK(launch_mean_resid(c, (const float2 *)d_y, (float2 *)d_ytil, c->m_max / c->nx));
+        if (c->general) CK(launch_mean_resid_general(c, (const float2 *)d_y, (float2 *)d_ytil));
+        else CK(launch_mean_resid(c, (const float2 *)d_y, (float2 *)d_ytil, c->m_max / c->nx));
     }
     lrccs_status s = sync_status(c);
     if (out_iters) *out_iters = it;
@@ -738,7 +774,8 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
-    "k_images", "k_cg_init", "k_cg_step", "k_mean_resid"};
+    "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_rows_gen",
+    "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

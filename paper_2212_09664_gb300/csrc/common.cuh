@@ -52,6 +52,13 @@ LRCCS_DEV int pair_index(int a, int b, int r) {  // a <= b
 }
 
 // Load the twiddle table of length N into shared memory.
+// |v|^2 in FP64 without contraction: the truncation decision |y|^2 <= gamma of
+// the spectral initialisation is taken on exactly the squares an FP64
+// reference forms.
+LRCCS_DEV double abs2_rn(float2 v) {
+    return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
+}
+
 LRCCS_DEV void load_twiddles(float2 *s_tw, const float2 *g_tw, int N) {
     for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = g_tw[t];
 }
@@ -429,6 +436,15 @@ LRCCS_DEV void cp_async8(void *dst, const void *src) {
 // 16-byte copy (two complex64); src and dst must be 16-byte aligned.
 LRCCS_DEV void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// Stage `count` complex64 values from global `src` into shared `dst`, 16 bytes
+// per copy when both are 16-byte aligned and count is even, else 8 bytes.
+LRCCS_DEV void stage_row(float2 *dst, const float2 *src, int count, int tid, int nthr) {
+    if (((((uintptr_t)src) | smem_u32(dst)) & 15) == 0 && (count & 1) == 0) {
+        for (int e = tid; e < count / 2; e += nthr) cp_async16(dst + 2 * e, src + 2 * e);
+    } else {
+        for (int e = tid; e < count; e += nthr) cp_async8(dst + e, src + e);
+    }
 }
 LRCCS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 LRCCS_DEV void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }

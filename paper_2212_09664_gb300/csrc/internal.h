@@ -27,6 +27,9 @@ enum {
     MT_MMIN = 2,    // min_k m_k
     MT_MMAX = 3,    // max_k m_k
     MT_RANK = 4,    // rank chosen by the init
+    MT_GENERAL = 5, // 1: some row is only partly sampled (general 2D masks)
+    MT_TOTAL = 6,   // sum_k m_k (samples per coil, all frames)
+    MT_NU = 7,      // n_u: k-space points sampled by at least one frame (general masks)
     MT_COUNT = 8
 };
 
@@ -38,7 +41,10 @@ enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_COUNT = 8 };
 enum {
     KID_ROWCOUNT = 0, KID_STRUCTURE, KID_FILL_IDX, KID_ENERGY, KID_INIT_ROWS, KID_INIT_COLS, KID_GRAM_X0,
     KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_ROW_GRAM, KID_SOLVE, KID_ROW_W, KID_ADJ_COLS,
-    KID_IMAGES, KID_CG_INIT, KID_CG_STEP, KID_MEAN_RESID, KID_COUNT
+    KID_IMAGES, KID_CG_INIT, KID_CG_STEP, KID_MEAN_RESID,
+    // general (2D) masks
+    KID_UNION, KID_FILL_GEN, KID_INIT_ROWS_GEN, KID_FWD_ROWS, KID_SAMPLE_GRAM, KID_SOLVE_GEN, KID_SAMPLE_W,
+    KID_ADJ_ROWS, KID_MEAN_RESID_GEN, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -63,7 +69,7 @@ struct lrccs_ctx {
     cudaGraphExec_t iter_exec;
     long long iter_counts[KID_COUNT];   // kernel launches per replay
     std::vector<prof_rec> iter_prof;    // timing events recorded by the graph
-    int iter_n, iter_r, iter_nused;
+    int iter_n, iter_r, iter_nused, iter_general, iter_nu;
     unsigned long long iter_mask;
     const void *iter_T;
     bool iter_graph_failed;             // capture not possible here: launch directly
@@ -87,6 +93,9 @@ struct lrccs_ctx {
     int n_lines;       // host copy of MT_NLINES
     int m_max;         // host copy of MT_MMAX (largest per-frame sample count per coil)
     int64_t total;     // fp[q] (samples per coil, all frames)
+    int general;       // the loaded masks have partly sampled rows: 2D transforms per iteration
+    int n_u;           // host copy of MT_NU (general masks)
+    size_t gen_cap_q;  // frames the general-mask buffers were allocated for (0: none yet)
     int dev_smem_optin;
     int test_timeout;  // lrccs_test_wait_timeout: the next direct k_gdqr launch waits for an unreachable barrier
     std::string err;
@@ -97,6 +106,10 @@ struct lrccs_ctx {
     int32_t *d_rowcnt;           // q * ny  samples of frame k in row ky
     int32_t *d_rowidx;           // q * ny  line index of row ky in frame k, or -1
     int32_t *d_framerows;        // q * ny  row ky of line i of frame k, at lineptr[k] + i
+    int32_t *d_framek;           // q * ny  frame k of frame row lineptr[k] + i
+    int32_t *d_mks;              // q       m_k, samples per coil of frame k
+    int32_t *d_fpk;              // q + 1   frame sample offsets (the running sum of m_k)
+    int32_t *d_rowoff;           // q * ny  first sample of (frame k, row ky) in the frame-ordered sample list
     int32_t *d_lineptr;          // q + 1
     int32_t *d_rfptr;            // ny + 1  frames sampling row ky: rflist[rfptr[ky] .. rfptr[ky+1])
     int32_t *d_rflist;           // q * ny
@@ -125,6 +138,22 @@ struct lrccs_ctx {
     double *d_gram;              // 2 * q * q  X0^H X0 (FP64 re, im)
     float2 *d_V;                 // q * q eigenvectors of X0^H X0 (columns, sorted)
     double2 *d_tot;              // k_gdqr totals: [U_t^H U_{t+1} (r*r) | h = U^H Z (q*r)] after a launch
+
+    // general (2D) masks: the union Omega_u of the frames' samples, kept row by
+    // row (points of row ky at u in [uptr[ky], uptr[ky+1]), ascending kx)
+    int32_t *d_ucnt;             // n       frames sampling k-space point i
+    int32_t *d_uloc;             // n       index of point i among its row's union points, or -1
+    int32_t *d_floc;             // n       offset of point i's frame list within its row
+    int32_t *d_urow;             // 2 * ny  union points and frame-list entries per row
+    int32_t *d_uptr;             // ny + 1
+    int32_t *d_ufrow;            // ny + 1
+    int32_t *d_upos;             // n       union index of point i, or -1
+    int32_t *d_uidx;             // n_u     k-space index of union point u
+    int32_t *d_ufptr;            // n_u + 1 frames sampling u: uflist[ufptr[u] .. ufptr[u+1])
+    int32_t *d_uflist;           // sum m_k
+    int32_t *d_fu;               // sum m_k union index of every frame sample (frame-ordered)
+    float2 *d_FU;                // nc * n_u * rmax  F(d_j o U) at the union points (FU[j][u][l])
+    float2 *d_Pu;                // n_u * npairs      coil-summed Gram of every union point
 };
 
 void set_err(lrccs_ctx *c, const char *fmt, ...);
@@ -135,6 +164,16 @@ void prof_end(lrccs_ctx *c, int kid);
 // cudaError_t of the launch.
 cudaError_t launch_twiddles(float2 *tw, int N, cudaStream_t s);
 cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d_fp_user);
+cudaError_t launch_fill_lines(lrccs_ctx *c);
+// general (2D) masks (kernels_general.cu)
+cudaError_t launch_compact_general(lrccs_ctx *c, const uint8_t *d_mask);
+cudaError_t launch_init_rows_general(lrccs_ctx *c, const float2 *d_y);
+cudaError_t launch_iteration_general_front(lrccs_ctx *c);   // forward rows + sample Grams + B-step
+cudaError_t launch_iteration_general_back(lrccs_ctx *c);    // W per sample + inverse rows
+cudaError_t launch_fwd_rows(lrccs_ctx *c);
+cudaError_t launch_sample_w(lrccs_ctx *c);
+cudaError_t launch_adj_rows(lrccs_ctx *c);
+cudaError_t launch_mean_resid_general(lrccs_ctx *c, const float2 *d_y, float2 *d_ytil);
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);
@@ -153,7 +192,7 @@ int npairs_of(int r);
 // Bits of the device status word ctx->d_status.
 enum {
     ST_FRAMEPTR_MISMATCH = 1 << 0,
-    ST_PARTIAL_ROWS = 1 << 1,
+    ST_RESERVED_1 = 1 << 1,   // unused
     ST_NOT_SPD_LS = 1 << 2,
     ST_NOT_SPD_QR = 1 << 3,
     ST_ZERO_SIGMA = 1 << 4,

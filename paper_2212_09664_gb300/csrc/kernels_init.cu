@@ -39,42 +39,64 @@ __global__ void k_rowcount(const uint8_t *__restrict__ mask, int rows, int nx, i
     if (lane == 0) rowcnt[w] = c;
 }
 
+// Per-frame and per-row structure of the masks from the per-(frame, row)
+// sample counts.  Rows of a frame with at least one sample are the frame's
+// "frame rows" (its lines, for 1D Cartesian masks): lineptr / framerows /
+// framek / rowidx.  Also the frames' sample counts m_k and offsets fpk (checked
+// against the caller's frame_ptr), each (frame, row)'s first sample rowoff, the
+// rows sampled by some frame, and meta[MT_GENERAL] = 1 when some row is only
+// partly sampled (a general 2D mask).
 __global__ void k_structure(const int32_t *__restrict__ rowcnt, const int64_t *__restrict__ fp_user,
-                            int q, int ny, int nx, int32_t *rowidx, int32_t *framerows,
+                            int q, int ny, int nx, int32_t *rowidx, int32_t *framerows, int32_t *framek,
                             int32_t *lineptr, int32_t *rfptr, int32_t *rflist, int32_t *usedrows,
-                            uint8_t *rowused, int32_t *meta, unsigned int *status, double *scal) {
+                            uint8_t *rowused, int32_t *mks, int32_t *fpk, int32_t *rowoff, int32_t *meta,
+                            unsigned int *status, double *scal) {
     __shared__ int s_lines[129];
+    __shared__ int s_m[129];
+    __shared__ int s_fp[130];
     __shared__ int s_rf[257];
+    __shared__ int s_partial;
     const int tid = threadIdx.x;
+    if (tid == 0) s_partial = 0;
+    __syncthreads();
     for (int k = tid; k < q; k += blockDim.x) {
-        int L = 0;
+        int L = 0, m = 0, part = 0;
         for (int ky = 0; ky < ny; ++ky) {
-            int c = rowcnt[k * ny + ky];
-            if (c == nx) ++L;
-            else if (c != 0) atomicOr(status, (unsigned)ST_PARTIAL_ROWS);
+            const int c = rowcnt[k * ny + ky];
+            L += c > 0;
+            m += c;
+            part |= (c != 0 && c != nx);
         }
         s_lines[k] = L;
+        s_m[k] = m;
+        if (part) s_partial = 1;
     }
     for (int ky = tid; ky < ny; ky += blockDim.x) {
         int c = 0;
-        for (int k = 0; k < q; ++k) c += (rowcnt[k * ny + ky] == nx);
+        for (int k = 0; k < q; ++k) c += (rowcnt[k * ny + ky] > 0);
         s_rf[ky] = c;
     }
     __syncthreads();
     if (tid == 0) {
-        int acc = 0, mmin = 0x7fffffff, mmax = 0;
+        int acc = 0, accm = 0, mmin = 0x7fffffff, mmax = 0;
         for (int k = 0; k < q; ++k) {
             lineptr[k] = acc;
-            int L = s_lines[k];
-            acc += L;
-            mmin = min(mmin, L * nx);
-            mmax = max(mmax, L * nx);
+            s_fp[k] = accm;
+            fpk[k] = accm;
+            acc += s_lines[k];
+            accm += s_m[k];
+            mmin = min(mmin, s_m[k]);
+            mmax = max(mmax, s_m[k]);
         }
         lineptr[q] = acc;
+        s_fp[q] = accm;
+        fpk[q] = accm;
         meta[MT_NLINES] = acc;
         meta[MT_MMIN] = mmin;
         meta[MT_MMAX] = mmax;
-        scal[SC_MBAR] = (double)acc * (double)nx / (double)q;
+        meta[MT_TOTAL] = accm;
+        meta[MT_GENERAL] = s_partial;
+        scal[SC_MBAR] = (double)accm / (double)q;
         int pacc = 0, nu = 0;
         for (int ky = 0; ky < ny; ++ky) {
             rfptr[ky] = pacc;
@@ -84,17 +106,22 @@ __global__ void k_structure(const int32_t *__restrict__ rowcnt, const int64_t *_
         }
         rfptr[ny] = pacc;
         meta[MT_NUSED] = nu;
-        if (fp_user[q] != (int64_t)acc * nx || fp_user[0] != 0) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
+        if (fp_user[q] != (int64_t)accm || fp_user[0] != 0) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
     }
     __syncthreads();
     for (int k = tid; k < q; k += blockDim.x) {
         const int base = lineptr[k];
-        if (fp_user[k] != (int64_t)base * nx) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
-        int i = 0;
+        if (fp_user[k] != (int64_t)s_fp[k]) atomicOr(status, (unsigned)ST_FRAMEPTR_MISMATCH);
+        mks[k] = s_m[k];
+        int i = 0, off = s_fp[k];
         for (int ky = 0; ky < ny; ++ky) {
-            if (rowcnt[k * ny + ky] == nx) {
+            const int c = rowcnt[k * ny + ky];
+            rowoff[k * ny + ky] = off;
+            off += c;
+            if (c > 0) {
                 rowidx[k * ny + ky] = i;
                 framerows[base + i] = ky;
+                framek[base + i] = k;
                 ++i;
             } else {
                 rowidx[k * ny + ky] = -1;
@@ -104,7 +131,7 @@ __global__ void k_structure(const int32_t *__restrict__ rowcnt, const int64_t *_
     for (int ky = tid; ky < ny; ky += blockDim.x) {
         int base = rfptr[ky], c = 0;
         for (int k = 0; k < q; ++k)
-            if (rowcnt[k * ny + ky] == nx) rflist[base + c++] = k;
+            if (rowcnt[k * ny + ky] > 0) rflist[base + c++] = k;
     }
 }
 
@@ -123,11 +150,17 @@ cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d
     prof_end(c, KID_ROWCOUNT);
     prof_begin(c, KID_STRUCTURE);
     k_structure<<<1, 256, 0, c->stream>>>(c->d_rowcnt, d_fp_user, c->q, c->ny, c->nx, c->d_rowidx,
-                                           c->d_framerows, c->d_lineptr, c->d_rfptr, c->d_rflist,
-                                           c->d_usedrows, c->d_rowused, c->d_meta, c->d_status, c->d_scal);
+                                           c->d_framerows, c->d_framek, c->d_lineptr, c->d_rfptr, c->d_rflist,
+                                           c->d_usedrows, c->d_rowused, c->d_mks, c->d_fpk, c->d_rowoff, c->d_meta,
+                                           c->d_status, c->d_scal);
     prof_end(c, KID_STRUCTURE);
+    return cudaGetLastError();
+}
+
+// Sample indices of masks that are unions of full lines (meta[MT_GENERAL] = 0).
+cudaError_t launch_fill_lines(lrccs_ctx *c) {
     prof_begin(c, KID_FILL_IDX);
-    k_fill_idx<<<rows, 128, 0, c->stream>>>(c->d_framerows, c->d_meta, c->nx, c->d_idx);
+    k_fill_idx<<<c->q * c->ny, 128, 0, c->stream>>>(c->d_framerows, c->d_meta, c->nx, c->d_idx);
     prof_end(c, KID_FILL_IDX);
     return cudaGetLastError();
 }
@@ -137,9 +170,6 @@ cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d
 // |y|^2 is formed in FP64 without contraction so that the truncation decision
 // |y|^2 <= gamma is taken on exactly the same squares as an FP64 reference.
 
-LRCCS_DEV double abs2_rn(float2 v) {
-    return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
-}
 
 __global__ void k_energy(const float2 *__restrict__ y, int64_t count, double trunc, double *part,
                          unsigned int *counter, double *scal) {
@@ -211,7 +241,8 @@ __global__ void __launch_bounds__(256) k_init_rows(const float2 *__restrict__ y,
 template <int P>
 __global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0, const float2 *__restrict__ smaps,
                                                     const int32_t *__restrict__ rowidx,
-                                                    const int32_t *__restrict__ lineptr, const double *__restrict__ scal,
+                                                    const int32_t *__restrict__ lineptr, const int32_t *__restrict__ mks,
+                                                    const double *__restrict__ scal,
                                                     float2 *__restrict__ Z, float2 *__restrict__ X0, int nx, int q,
                                                     int nc, const float2 *__restrict__ g_tw, float scale) {
     constexpr int NY = 32 * P;
@@ -266,7 +297,8 @@ __global__ void __launch_bounds__(256) k_init_cols(const float2 *__restrict__ T0
         }
     }
     const double mbar = scal[SC_MBAR];
-    const float xs = (mk > 0) ? (float)(1.0 / sqrt((double)mk * mbar)) : 0.f;
+    const int msamp = mks[k];   // samples per coil of frame k (m_k of Alg. 2's scale 1/sqrt(m_k mbar))
+    const float xs = (msamp > 0) ? (float)(1.0 / sqrt((double)msamp * mbar)) : 0.f;
 #pragma unroll
     for (int u = 0; u < ACC; ++u) {
         const int e = threadIdx.x + 256 * u;
@@ -297,7 +329,10 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const float sy = (float)(1.0 / sqrt((double)c->ny));
     const unsigned rb = (unsigned)((total_rows + 3) / 4);
-    if (total_rows > 0) {
+    if (c->general) {   // frame rows hold scattered samples: scatter, then the row transforms
+        cudaError_t eg = launch_init_rows_general(c, d_y);
+        if (eg != cudaSuccess) return eg;
+    } else if (total_rows > 0) {
         DISPATCH_P(c->px, {
             prof_begin(c, KID_INIT_ROWS);
             k_init_rows<P_><<<rb, 256, 0, c->stream>>>(d_y, c->d_T, total_rows, c->d_scal, c->d_twx, sx);
@@ -310,7 +345,7 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
     dim3 grid(c->nx / TXI, c->q);
     DISPATCH_P(c->py, {
         prof_begin(c, KID_INIT_COLS);
-        k_init_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowidx, c->d_lineptr,
+        k_init_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_smaps, c->d_rowidx, c->d_lineptr, c->d_mks,
                                                         c->d_scal, c->d_Z, c->d_X0, c->nx, c->q, c->nc,
                                                         c->d_twy, sy);
         prof_end(c, KID_INIT_COLS);

@@ -49,16 +49,6 @@ namespace cg = cooperative_groups;
 
 int npairs_of(int r) { return r * (r + 1) / 2; }
 
-// Stage `count` complex64 values from global `src` into shared `dst`, 16 bytes
-// per copy when both are 16-byte aligned and count is even, else 8 bytes.
-LRCCS_DEV void stage_row(float2 *dst, const float2 *src, int count, int tid, int nthr) {
-    if (((((uintptr_t)src) | smem_u32(dst)) & 15) == 0 && (count & 1) == 0) {
-        for (int e = tid; e < count / 2; e += nthr) cp_async16(dst + 2 * e, src + 2 * e);
-    } else {
-        for (int e = tid; e < count; e += nthr) cp_async8(dst + e, src + e);
-    }
-}
-
 // ---------------------------------------------------------------- A: forward, along y
 
 template <int P>
@@ -463,10 +453,17 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
     cudaError_t el = launch_fwd_cols(c);   // A
     if (el != cudaSuccess) return el;
-    el = launch_row_gram(c);               // B
-    if (el != cudaSuccess) return el;
-    launch_solve(c);                       // C
-    launch_row_w(c);                       // D
+    if (c->general) {                      // 2D masks: x transforms, per-point Grams and W (kernels_general.cu)
+        el = launch_iteration_general_front(c);
+        if (el != cudaSuccess) return el;
+        el = launch_iteration_general_back(c);
+        if (el != cudaSuccess) return el;
+    } else {
+        el = launch_row_gram(c);           // B
+        if (el != cudaSuccess) return el;
+        launch_solve(c);                   // C
+        launch_row_w(c);                   // D
+    }
     el = launch_adj_cols(c);               // E
     if (el != cudaSuccess) return el;
     cudaError_t e = cudaGetLastError();
@@ -482,17 +479,29 @@ cudaError_t launch_normal_op(lrccs_ctx *c) {
     if (c->r != 1) return cudaErrorInvalidValue;
     cudaError_t el = launch_fwd_cols(c);
     if (el != cudaSuccess) return el;
-    launch_row_w(c);
+    if (c->general) {   // W_u = number of frames sampling point u
+        el = launch_fwd_rows(c);
+        if (el == cudaSuccess) el = launch_sample_w(c);
+        if (el == cudaSuccess) el = launch_adj_rows(c);
+        if (el != cudaSuccess) return el;
+    } else {
+        launch_row_w(c);
+    }
     el = launch_adj_cols(c);
     if (el != cudaSuccess) return el;
     return cudaGetLastError();
 }
 
-// d_T <- F_y(d_j o U) on the sampled rows (the first step of an iteration).
+// d_T <- F_y(d_j o U) on the sampled rows (the first step of an iteration);
+// with general masks also d_FU <- F(d_j o U) at the union points.
 cudaError_t launch_fwd_only(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
     cudaError_t el = launch_fwd_cols(c);
     if (el != cudaSuccess) return el;
+    if (c->general) {
+        el = launch_fwd_rows(c);
+        if (el != cudaSuccess) return el;
+    }
     return cudaGetLastError();
 }
 

@@ -12,22 +12,12 @@
 #define RMAXC 16   // compile-time bound on the rank
 #define NT 256     // threads per block
 
+// The Cholesky solve of one frame's r x r system from its Gram pairs sP (FP64
+// sums) and h_k (totals of k_gdqr), by the block's first warp.
 template <int R>
-__global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, const double2 *__restrict__ htot,
-                                              const int32_t *__restrict__ lineptr,
-                                              const int32_t *__restrict__ framerows, float2 *__restrict__ B,
-                                              unsigned int *status) {
-    constexpr int np = R * (R + 1) / 2, rr = R * R;
-    __shared__ double sP[2 * np];
-    __shared__ float2 sG[rr];
-    __shared__ float sinv[R];
-    __shared__ int s_rows[256];
-    const int k = blockIdx.x;
-    const int lp = lineptr[k], L = lineptr[k + 1] - lp;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) s_rows[i] = framerows[lp + i];
-    __syncthreads();
-    // G_k pairs: sum over the frame's rows of the coil-summed row Grams
-    block_sum(np, L, sP, [=](int p, int i) { return __ldg(Prow + (size_t)s_rows[i] * np + p); });
+static __device__ void solve_frame(const double *sP, float2 *sG, float *sinv, bool any, const double2 *htot, int k,
+                                   float2 *B, unsigned int *status) {
+    constexpr int rr = R * R;
     for (int e = threadIdx.x; e < rr; e += blockDim.x) {
         const int a = e / R, b = e - a * R;
         const int p = a <= b ? pair_index(a, b, R) : pair_index(b, a, R);
@@ -36,7 +26,7 @@ __global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, c
     __syncthreads();
     if ((threadIdx.x >> 5) != 0) return;
     const int lane = threadIdx.x & 31;
-    const bool ok = (L > 0) && warp_chol32<R>(sG, R, sinv);
+    const bool ok = any && warp_chol32<R>(sG, R, sinv);
     float2 h = make_float2(0.f, 0.f);
     if (lane < R) {
         const double2 v = __ldcg(htot + rr + (size_t)k * R + lane);
@@ -48,6 +38,43 @@ __global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, c
     if (lane < R) B[(size_t)k * R + lane] = x;
 }
 
+// Line masks: G_k = sum over the frame's sampled rows of the row Grams P[ky].
+template <int R>
+__global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, const double2 *__restrict__ htot,
+                                              const int32_t *__restrict__ lineptr,
+                                              const int32_t *__restrict__ framerows, float2 *__restrict__ B,
+                                              unsigned int *status) {
+    constexpr int np = R * (R + 1) / 2;
+    __shared__ double sP[2 * np];
+    __shared__ float2 sG[R * R];
+    __shared__ float sinv[R];
+    __shared__ int s_rows[256];
+    const int k = blockIdx.x;
+    const int lp = lineptr[k], L = lineptr[k + 1] - lp;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) s_rows[i] = framerows[lp + i];
+    __syncthreads();
+    // G_k pairs: sum over the frame's rows of the coil-summed row Grams
+    block_sum(np, L, sP, [=](int p, int i) { return __ldg(Prow + (size_t)s_rows[i] * np + p); });
+    solve_frame<R>(sP, sG, sinv, L > 0, htot, k, B, status);
+}
+
+// General masks: G_k = sum over the frame's samples s of the point Grams
+// P_{u(s)} (u(s) = fu[s], the union index of sample s).
+template <int R>
+__global__ void __launch_bounds__(NT) k_solve_gen(const float2 *__restrict__ Pu, const double2 *__restrict__ htot,
+                                                  const int32_t *__restrict__ fpk, const int32_t *__restrict__ fu,
+                                                  float2 *__restrict__ B, unsigned int *status) {
+    constexpr int np = R * (R + 1) / 2;
+    __shared__ double sP[2 * np];
+    __shared__ float2 sG[R * R];
+    __shared__ float sinv[R];
+    const int k = blockIdx.x;
+    const int f0 = fpk[k], m = fpk[k + 1] - f0;
+    const int32_t *fk = fu + f0;
+    block_sum(np, m, sP, [=](int p, int i) { return __ldg(Pu + (size_t)__ldg(fk + i) * np + p); });
+    solve_frame<R>(sP, sG, sinv, m > 0, htot, k, B, status);
+}
+
 typedef void (*solve_kernel_t)(const float2 *, const double2 *, const int32_t *, const int32_t *, float2 *,
                                unsigned int *);
 static const solve_kernel_t kSolve[RMAXC] = {k_solve<1>,  k_solve<2>,  k_solve<3>,  k_solve<4>,
@@ -55,8 +82,21 @@ static const solve_kernel_t kSolve[RMAXC] = {k_solve<1>,  k_solve<2>,  k_solve<3
                                              k_solve<9>,  k_solve<10>, k_solve<11>, k_solve<12>,
                                              k_solve<13>, k_solve<14>, k_solve<15>, k_solve<16>};
 
+typedef void (*solve_gen_t)(const float2 *, const double2 *, const int32_t *, const int32_t *, float2 *,
+                            unsigned int *);
+static const solve_gen_t kSolveGen[RMAXC] = {k_solve_gen<1>,  k_solve_gen<2>,  k_solve_gen<3>,  k_solve_gen<4>,
+                                             k_solve_gen<5>,  k_solve_gen<6>,  k_solve_gen<7>,  k_solve_gen<8>,
+                                             k_solve_gen<9>,  k_solve_gen<10>, k_solve_gen<11>, k_solve_gen<12>,
+                                             k_solve_gen<13>, k_solve_gen<14>, k_solve_gen<15>, k_solve_gen<16>};
+
 cudaError_t launch_solve(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    if (c->general) {
+        prof_begin(c, KID_SOLVE_GEN);
+        kSolveGen[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_Pu, c->d_tot, c->d_fpk, c->d_fu, c->d_B, c->d_status);
+        prof_end(c, KID_SOLVE_GEN);
+        return cudaGetLastError();
+    }
     prof_begin(c, KID_SOLVE);
     kSolve[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_P, c->d_tot, c->d_lineptr,
                                                  c->d_framerows, c->d_B, c->d_status);

@@ -331,6 +331,10 @@ WORKLOADS = {
     # cardiac-shaped multi-coil phantom, 8x variable-density Cartesian
     "cardiac192_q48_c12_r10": dict(kind="phantom", ny=192, nx=192, q=48, nc=12, rank=10, t_iter=50,
                                    accel=8.0, noise=0.01),
+    # the same phantom with a contrast-uptake ramp per region, 20 coils, 16
+    # golden-angle pseudo-radial spokes per frame on the Cartesian grid
+    "radial256_q64_c20_r12": dict(kind="phantom", ny=256, nx=256, q=64, nc=20, rank=12, t_iter=50,
+                                  mask_kind="radial", spokes=16, noise=0.01, ramp=True),
 }
 
 
