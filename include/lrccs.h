@@ -33,9 +33,11 @@
  *                 lrccs_iterate when info is requested).
  *
  * Scope of this build: images with ny, nx multiples of 32 in [32, 256];
- * rank r <= 16; q <= 128 frames; C <= 64 coils; every frame's mask must be a
- * union of full phase-encode lines (1D Cartesian sampling, Sec. V); other
- * masks return LRCCS_E_UNSUPPORTED.
+ * rank r <= 16; q <= 128 frames; C <= 64 coils.  Masks are arbitrary sample
+ * sets on the Cartesian grid.  Masks whose rows are either fully sampled or
+ * empty (1D Cartesian lines, Sec. V) take a faster path with no x-direction
+ * transforms; any other mask (pseudo-radial spokes gridded onto the grid,
+ * scattered samples) takes the general path with full 2D transforms.
  */
 #ifndef LRCCS_H
 #define LRCCS_H
@@ -108,10 +110,11 @@ lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params,
  * Compacts the masks, computes gamma, Z = [A_k^H y_k] and the truncated and
  * scaled X0, its top-r left singular vectors U_0, and resets t and eta.  The
  * call blocks until the device work is done.  Inputs are not retained.
+ * The first general (2D) mask a context sees allocates that path's buffers
+ * (about 2 q n int32 plus C n rank_max complex64).
  * Errors: LRCCS_E_INVALID (frame_ptr inconsistent with the mask, or a fixed
  * rank above q: the top-r singular vectors of the n x q X0 need r <= q),
- * LRCCS_E_UNSUPPORTED (a mask that is not a union of full lines),
- * LRCCS_E_RANK_DEFICIENT (sigma_r(X0) = 0), LRCCS_E_CUDA. */
+ * LRCCS_E_RANK_DEFICIENT (sigma_r(X0) = 0), LRCCS_E_NOMEM, LRCCS_E_CUDA. */
 lrccs_status lrccs_init(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
                         const uint8_t *d_mask, const void *d_smaps, int32_t *out_rank);
 
@@ -176,6 +179,56 @@ lrccs_status lrccs_get_buffer(lrccs_ctx *ctx, lrccs_buffer which, void *d_dst, s
 lrccs_status lrccs_mean_step(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
                              const uint8_t *d_mask, const void *d_smaps, double tol, int32_t max_iter,
                              void *d_zbar, void *d_ytil, int32_t *out_iters);
+
+/* ---- Model-error correction (Alg. 3) ------------------------------------------
+ * Alg. 1 follows Alg. 2 by estimating, frame by frame, what the rank-r model
+ * misses: with ytt_k = y~_k - A_k x_k the residual measurements of the last
+ * iterate x_k = U_{t-1} b_k (y~ = the data the context was initialised with,
+ * usually the mean-subtracted output of lrccs_mean_step),
+ *   MEC-1 (unstructured): e_k from `iters` CGLS iterations on
+ *          min_e ||ytt_k - A_k e||^2 from e = 0 (the paper: 3 iterations; its
+ *          tolerance 1e-36 never stops them early);
+ *   MEC-2 (sparse in the temporal Fourier domain): ISTA from E_0 = 0: step tau
+ *          forms M_tau = F_t(E_tau + A^H(ytt - A E_tau)) (F_t the unitary DFT
+ *          along the q frames), sets omega = omega_frac max|M_0| at tau = 0, and
+ *          E_{tau+1} = F_t^{-1} SThr_omega(M_tau) (complex soft threshold
+ *          m (|m| - omega)/|m| above omega, else 0); it stops after max_iter
+ *          updates or once ||M_tau - M_{tau-1}||_F < rel_change ||M_{tau-1}||_F
+ *          (the paper: 10, 0.0025, 0.001).
+ * Both need a context after at least one lrccs_iterate (or lrccs_online_frames).
+ *   d_zbar : NULL, or device complex64 n entries: the mean added into d_X
+ *   d_E    : NULL, or device complex64 q x n (row k = e_k), receives E
+ *   d_X    : NULL, or device complex64 q x n, receives x_k = zbar + U_{t-1} b_k + e_k
+ *   out_iters (MEC-2): NULL, or the number of ISTA updates made
+ * The frames are processed rank_max at a time through the per-frame normal
+ * operators A_k^H A_k (the iteration's transforms with each frame's own
+ * sampling between them).  The first call allocates 5 q n complex64 of work
+ * space in the context.  Both calls synchronise (MEC-2 reads its stopping test
+ * after every step).  Errors: LRCCS_E_STATE (no iterate yet), LRCCS_E_INVALID,
+ * LRCCS_E_NOMEM, LRCCS_E_CUDA. */
+lrccs_status lrccs_mec1(lrccs_ctx *ctx, int32_t iters, const void *d_zbar, void *d_E, void *d_X);
+lrccs_status lrccs_mec2(lrccs_ctx *ctx, int32_t max_iter, double rel_change, double omega_frac,
+                        const void *d_zbar, void *d_E, void *d_X, int32_t *out_iters);
+
+/* ---- Online subspace tracking (Alg. 5) ----------------------------------------
+ * After the first mini-batch (solved by Alg. 1: mean step, Alg. 2, MEC), Alg. 5
+ * keeps that mini-batch's mean zbar and subspace U fixed and reconstructs every
+ * later frame on its own: y~_k = y_k - A_k zbar, b_k = (A_k U)^+ y~_k, e_k from
+ * mec_iters CGLS iterations on y~_k - A_k U b_k (MEC-1), x_k = zbar + U b_k + e_k.
+ * One call reconstructs the context's q frames (q = the number of frames per
+ * call) from the subspace set by lrccs_set_subspace / lrccs_set_state (one
+ * Cholesky QR pass of it first, which changes an orthonormal U by rounding
+ * only).
+ *   d_y, d_frame_ptr, d_mask, d_smaps : the frames, as for lrccs_init
+ *   d_zbar   : device complex64, n entries (the first mini-batch's mean)
+ *   mec_iters: CGLS iterations of MEC-1 (3 in the paper), 0 .. 1000
+ *   d_X      : NULL, or device complex64 q x n (row k = x_k)
+ *   d_B      : NULL, or device complex64 r x q (b_k contiguous)
+ * The call synchronises.  Errors: LRCCS_E_STATE (no subspace), LRCCS_E_INVALID,
+ * LRCCS_E_RANK_DEFICIENT, LRCCS_E_NOMEM, LRCCS_E_CUDA. */
+lrccs_status lrccs_online_frames(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
+                                 const uint8_t *d_mask, const void *d_smaps, const void *d_zbar,
+                                 int32_t mec_iters, void *d_X, void *d_B);
 
 /* ---- Mini-batch subspace tracking (Alg. 4) ----------------------------------
  * Alg. 4 reconstructs a long acquisition one mini-batch of consecutive frames

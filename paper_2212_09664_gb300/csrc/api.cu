@@ -70,7 +70,8 @@ static void free_all(lrccs_ctx *c) {
                     c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
                     c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot, c->d_framek,
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
-                    c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu};
+                    c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
+                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -154,10 +155,12 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
               dalloc(c, &c->d_Up, (size_t)n * rmax) && dalloc(c, &c->d_G, (size_t)n * rmax) &&
               dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)ny * npm) &&
               dalloc(c, &c->d_gpart, gcap) && dalloc(c, &c->d_tot, gd_len) &&
-              dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)2 * q * q) &&
-              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_framek, (size_t)q * ny) &&
+              dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)6 * q * q) &&
+              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_Q, (size_t)q * q) &&
+              dalloc(c, &c->d_framek, (size_t)q * ny) &&
               dalloc(c, &c->d_mks, (size_t)q) && dalloc(c, &c->d_fpk, (size_t)q + 1) &&
-              dalloc(c, &c->d_rowoff, (size_t)q * ny);
+              dalloc(c, &c->d_rowoff, (size_t)q * ny) && dalloc(c, &c->d_maskc, (size_t)q * n) &&
+              dalloc(c, &c->d_twq, (size_t)q);
     if (!ok) {
         g_create_err = c->err;
         free_all(c);
@@ -175,6 +178,7 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
+    if (e == cudaSuccess) e = launch_twiddles(c->d_twq, q, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, CNT_COUNT * sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_scal, 0, SC_COUNT * sizeof(double), c->stream);
@@ -267,6 +271,7 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     CK(cudaMemsetAsync(c->d_meta, 0, MT_COUNT * sizeof(int32_t), c->stream));
     CK(cudaMemcpyAsync(c->d_smaps, d_smaps, (size_t)c->nc * c->n * sizeof(float2), cudaMemcpyDeviceToDevice,
                        c->stream));
+    CK(cudaMemcpyAsync(c->d_maskc, d_mask, (size_t)c->q * c->n, cudaMemcpyDeviceToDevice, c->stream));
     CK(launch_compact(c, d_mask, d_frame_ptr));
     lrccs_status s = sync_status(c);
     if (s != LRCCS_OK) return s;
@@ -628,6 +633,158 @@ extern "C" lrccs_status lrccs_mean_step(lrccs_ctx *c, const void *d_y, const int
     return s;
 }
 
+// ---------------------------------------------------------------- model-error correction (Alg. 3)
+
+static lrccs_status mec_ensure(lrccs_ctx *c) {
+    if (c->d_mec) return LRCCS_OK;
+    const int w = c->rmax, nch = (c->q + w - 1) / w;
+    if (!dalloc(c, &c->d_mec, (size_t)5 * nch * c->n * w) || !dalloc(c, &c->d_mscal, mec_scal_count(c->n, c->q, w)) ||
+        !dalloc(c, &c->d_mout, 8)) {
+        if (c->d_mec) cudaFree(c->d_mec);
+        if (c->d_mscal) cudaFree(c->d_mscal);
+        c->d_mec = nullptr;
+        c->d_mscal = nullptr;
+        return LRCCS_E_NOMEM;
+    }
+    c->mec_w = w;
+    c->mec_nch = nch;
+    return LRCCS_OK;
+}
+
+static float2 *mec_vec(lrccs_ctx *c, int which) {   // 0 E, 1 S, 2 P, 3 W, 4 M_prev
+    return c->d_mec + (size_t)which * c->mec_nch * c->n * c->mec_w;
+}
+
+// dst = [N_k src_k]_k, chunk by chunk
+static lrccs_status mec_normal(lrccs_ctx *c, const float2 *src, float2 *dst) {
+    const size_t cs = (size_t)c->n * c->mec_w;
+    for (int cc = 0; cc < c->mec_nch; ++cc)
+        CK(launch_frame_normal_op(c, src + cc * cs, dst + cc * cs, c->mec_w, cc * c->mec_w));
+    return LRCCS_OK;
+}
+
+// s_k = A_k^H ytt_k = Z[:, k] - N_k (U_{t-1} b_k) into S, P = S, E = 0, gamma_k = ||s_k||^2
+static lrccs_status mec_start(lrccs_ctx *c) {
+    float2 *P = mec_vec(c, 2), *W = mec_vec(c, 3);
+    CK(launch_mec_x(c, c->d_Uprev, nullptr, P));
+    lrccs_status s = mec_normal(c, P, W);
+    if (s != LRCCS_OK) return s;
+    CK(launch_mec_cg(c, 0, W));
+    return LRCCS_OK;
+}
+
+// `iters` CGLS iterations per frame (normal-equation form) from e = 0
+static lrccs_status mec1_run(lrccs_ctx *c, int iters) {
+    lrccs_status s = mec_start(c);
+    if (s != LRCCS_OK) return s;
+    for (int it = 0; it < iters; ++it) {
+        s = mec_normal(c, mec_vec(c, 2), mec_vec(c, 3));   // W = N P
+        if (s != LRCCS_OK) return s;
+        CK(launch_mec_cg(c, 1, nullptr));   // alpha
+        CK(launch_mec_cg(c, 2, nullptr));   // E, S, beta
+        CK(launch_mec_cg(c, 3, nullptr));   // P
+    }
+    return LRCCS_OK;
+}
+
+static lrccs_status mec_check(lrccs_ctx *c, const char *who) {
+    if (!c->initialized || c->t < 1 || c->need_h) {
+        set_err(c, "%s: run at least one iteration (or an online call) first", who);
+        return LRCCS_E_STATE;
+    }
+    return mec_ensure(c);
+}
+
+extern "C" lrccs_status lrccs_mec1(lrccs_ctx *c, int32_t iters, const void *d_zbar, void *d_E, void *d_X) {
+    if (!c) return LRCCS_E_INVALID;
+    if (iters < 0 || iters > 1000) {
+        set_err(c, "lrccs_mec1: iters outside [0, 1000]");
+        return LRCCS_E_INVALID;
+    }
+    lrccs_status s = mec_check(c, "lrccs_mec1");
+    if (s != LRCCS_OK) return s;
+    s = mec1_run(c, iters);
+    if (s != LRCCS_OK) return s;
+    CK(launch_mec_out(c, mec_vec(c, 0), (const float2 *)d_zbar, (float2 *)d_E, (float2 *)d_X));
+    return sync_status(c);
+}
+
+extern "C" lrccs_status lrccs_mec2(lrccs_ctx *c, int32_t max_iter, double rel_change, double omega_frac,
+                                   const void *d_zbar, void *d_E, void *d_X, int32_t *out_iters) {
+    if (!c) return LRCCS_E_INVALID;
+    if (max_iter < 0 || max_iter > 1000 || !(rel_change >= 0.0) || !(omega_frac >= 0.0)) {
+        set_err(c, "lrccs_mec2: max_iter outside [0, 1000], or a negative rel_change / omega_frac");
+        return LRCCS_E_INVALID;
+    }
+    lrccs_status s = mec_check(c, "lrccs_mec2");
+    if (s != LRCCS_OK) return s;
+    s = mec_start(c);   // S = s_0 = A^H ytt, E = 0
+    if (s != LRCCS_OK) return s;
+    float2 *E = mec_vec(c, 0), *S0 = mec_vec(c, 1), *V = mec_vec(c, 3);
+    float2 *M = mec_vec(c, 2), *Mprev = mec_vec(c, 4);
+    double omega = 0.0, h[3];
+    int tau = 0;
+    while (tau < max_iter) {
+        if (tau > 0) {   // V = N E (E = 0 at tau = 0)
+            s = mec_normal(c, E, V);
+            if (s != LRCCS_OK) return s;
+        }
+        CK(launch_tdft_fwd(c, E, S0, tau > 0 ? V : nullptr, tau > 0 ? Mprev : nullptr, M, c->d_mout));
+        CK(cudaMemcpyAsync(h, c->d_mout, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (tau == 0) omega = omega_frac * h[0];
+        else if (sqrt(h[1]) < rel_change * sqrt(h[2])) break;
+        CK(launch_tdft_inv(c, M, (float)omega, E));
+        float2 *t = M;
+        M = Mprev;
+        Mprev = t;
+        ++tau;
+    }
+    if (out_iters) *out_iters = tau;
+    CK(launch_mec_out(c, E, (const float2 *)d_zbar, (float2 *)d_E, (float2 *)d_X));
+    return sync_status(c);
+}
+
+// ---------------------------------------------------------------- online subspace tracking (Alg. 5)
+
+extern "C" lrccs_status lrccs_online_frames(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr,
+                                            const uint8_t *d_mask, const void *d_smaps, const void *d_zbar,
+                                            int32_t mec_iters, void *d_X, void *d_B) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps || !d_zbar || mec_iters < 0 || mec_iters > 1000) {
+        set_err(c, "lrccs_online_frames: null input pointer or mec_iters outside [0, 1000]");
+        return LRCCS_E_INVALID;
+    }
+    if (!c->has_u) {
+        set_err(c, "lrccs_online_frames: no subspace (lrccs_set_subspace or lrccs_set_state first)");
+        return LRCCS_E_STATE;
+    }
+    c->initialized = 0;
+    lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, false);
+    if (s != LRCCS_OK) return s;
+    s = mec_ensure(c);
+    if (s != LRCCS_OK) return s;
+    // A_k^H y~_k = Z[:, k] - N_k zbar  (y~_k = y_k - A_k zbar)
+    float2 *P = mec_vec(c, 2), *W = mec_vec(c, 3);
+    CK(launch_mec_x(c, nullptr, (const float2 *)d_zbar, P));
+    s = mec_normal(c, P, W);
+    if (s != LRCCS_OK) return s;
+    CK(launch_mec_subz(c, W));
+    // U fixed: re-orthonormalise it (rounding only), h_k = U^H A_k^H y~_k, and the B-step
+    s = warm_start(c);
+    if (s != LRCCS_OK) return s;
+    CK(launch_bstep(c));
+    c->t = 1;
+    c->initialized = 1;
+    // MEC-1 on ytt_k = y~_k - A_k U b_k, then x_k = zbar + U b_k + e_k
+    s = mec1_run(c, mec_iters);
+    if (s != LRCCS_OK) return s;
+    CK(launch_mec_out(c, mec_vec(c, 0), (const float2 *)d_zbar, nullptr, (float2 *)d_X));
+    if (d_B) CK(cudaMemcpyAsync(d_B, c->d_B, (size_t)c->q * c->r * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                c->stream));
+    return sync_status(c);
+}
+
 // State buffer: this header, then U (n x r complex64).
 struct state_header {
     uint32_t magic, version;
@@ -775,7 +932,8 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_rows_gen",
-    "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen"};
+    "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
+    "k_mec_elem", "k_mec_tdft"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

@@ -44,7 +44,9 @@ enum {
     KID_IMAGES, KID_CG_INIT, KID_CG_STEP, KID_MEAN_RESID,
     // general (2D) masks
     KID_UNION, KID_FILL_GEN, KID_INIT_ROWS_GEN, KID_FWD_ROWS, KID_SAMPLE_GRAM, KID_SOLVE_GEN, KID_SAMPLE_W,
-    KID_ADJ_ROWS, KID_MEAN_RESID_GEN, KID_COUNT
+    KID_ADJ_ROWS, KID_MEAN_RESID_GEN,
+    // model-error correction (Alg. 3) and online tracking (Alg. 5)
+    KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -135,8 +137,9 @@ struct lrccs_ctx {
     float2 *d_gpart;             // partial sums of the grid reductions (init kernels, k_gdqr)
     size_t gpart_cap;
     double *d_sigma;             // q
-    double *d_gram;              // 2 * q * q  X0^H X0 (FP64 re, im)
-    float2 *d_V;                 // q * q eigenvectors of X0^H X0 (columns, sorted)
+    double *d_gram;              // 3 x 2 q q: X0^H X0, A V0, V0^H A V0 (FP64 re, im)
+    float2 *d_V;                 // q * q eigenvectors of X0^H X0 (columns)
+    float2 *d_Q;                 // q * q rotations of the eigensolver's refine pass
     double2 *d_tot;              // k_gdqr totals: [U_t^H U_{t+1} (r*r) | h = U^H Z (q*r)] after a launch
 
     // general (2D) masks: the union Omega_u of the frames' samples, kept row by
@@ -154,6 +157,15 @@ struct lrccs_ctx {
     int32_t *d_fu;               // sum m_k union index of every frame sample (frame-ordered)
     float2 *d_FU;                // nc * n_u * rmax  F(d_j o U) at the union points (FU[j][u][l])
     float2 *d_Pu;                // n_u * npairs      coil-summed Gram of every union point
+
+    // model-error correction (Alg. 3): frames in chunks of mec_w = rank_max
+    // columns, vectors V[c][i][l] (frame c mec_w + l)
+    uint8_t *d_maskc;            // q * n   copy of the loaded masks (per-frame sampling inside N_k)
+    float2 *d_mec;               // 5 vectors of mec_nch * n * mec_w: E, S, P, W, and M_prev (MEC-2)
+    double *d_mscal;             // gamma, alpha, beta (q each), then reduction partials
+    double *d_mout;              // 8 FP64 results of the MEC-2 reductions
+    float2 *d_twq;               // q twiddles exp(-2 pi i t / q) of the temporal DFT
+    int mec_w, mec_nch;
 };
 
 void set_err(lrccs_ctx *c, const char *fmt, ...);
@@ -171,9 +183,24 @@ cudaError_t launch_init_rows_general(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_iteration_general_front(lrccs_ctx *c);   // forward rows + sample Grams + B-step
 cudaError_t launch_iteration_general_back(lrccs_ctx *c);    // W per sample + inverse rows
 cudaError_t launch_fwd_rows(lrccs_ctx *c);
+cudaError_t launch_fwd_rows_r(lrccs_ctx *c, int r);
+cudaError_t launch_adj_rows_r(lrccs_ctx *c, int r);
+cudaError_t launch_fwd_cols_on(lrccs_ctx *c, const float2 *src, int r);   // T <- F_y(d_j o src) (n x r src)
+cudaError_t launch_adj_cols_to(lrccs_ctx *c, float2 *dst, int r);         // dst <- sum_j conj(d_j) F_y^H T_j
 cudaError_t launch_sample_w(lrccs_ctx *c);
 cudaError_t launch_adj_rows(lrccs_ctx *c);
 cudaError_t launch_mean_resid_general(lrccs_ctx *c, const float2 *d_y, float2 *d_ytil);
+// model-error correction and online tracking (kernels_mec.cu)
+cudaError_t launch_frame_normal_op(lrccs_ctx *c, const float2 *src, float2 *dst, int w, int k0);
+cudaError_t launch_mec_x(lrccs_ctx *c, const float2 *Uprev, const float2 *zbar, float2 *X);
+cudaError_t launch_mec_subz(lrccs_ctx *c, const float2 *V);
+cudaError_t launch_mec_cg(lrccs_ctx *c, int kind, const float2 *V);
+cudaError_t launch_mec_out(lrccs_ctx *c, const float2 *E, const float2 *zbar, float2 *Eout, float2 *Xout);
+cudaError_t launch_tdft_fwd(lrccs_ctx *c, const float2 *E, const float2 *S0, const float2 *V, const float2 *Mprev,
+                            float2 *M, double *out);
+cudaError_t launch_tdft_inv(lrccs_ctx *c, const float2 *M, float omega, float2 *E);
+size_t mec_scal_count(int n, int q, int w);
+cudaError_t launch_bstep(lrccs_ctx *c);   // B-step only (forward transforms, Grams, solve) at the current U
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);

@@ -454,8 +454,7 @@ typedef void (*sw_t)(float2 *, const float2 *, const int32_t *, const int32_t *,
 static const sgram_t kSampleGram[RMAXC] = RANK_TABLE(k_sample_gram);
 static const sw_t kSampleW[RMAXC] = RANK_TABLE(k_sample_w);
 
-cudaError_t launch_fwd_rows(lrccs_ctx *c) {
-    const int r = c->r;
+cudaError_t launch_fwd_rows_r(lrccs_ctx *c, int r) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const size_t smem = ((size_t)2 * c->nx * r + c->nx) * sizeof(float2);
     dim3 grid(c->n_used, row_groups(c->nc));
@@ -486,8 +485,7 @@ cudaError_t launch_sample_w(lrccs_ctx *c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_rows(lrccs_ctx *c) {
-    const int r = c->r;
+cudaError_t launch_adj_rows_r(lrccs_ctx *c, int r) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const size_t smem = ((size_t)c->nx * r + c->nx) * sizeof(float2);
     dim3 grid(c->n_used, row_groups(c->nc));
@@ -499,6 +497,9 @@ cudaError_t launch_adj_rows(lrccs_ctx *c) {
     });
     return cudaGetLastError();
 }
+
+cudaError_t launch_fwd_rows(lrccs_ctx *c) { return launch_fwd_rows_r(c, c->r); }
+cudaError_t launch_adj_rows(lrccs_ctx *c) { return launch_adj_rows_r(c, c->r); }
 
 cudaError_t launch_iteration_general_front(lrccs_ctx *c) {
     cudaError_t e = launch_fwd_rows(c);

@@ -446,27 +446,49 @@ __global__ void __launch_bounds__(256) k_gram_sum(const float2 *__restrict__ par
     }
 }
 
-// One block: eigendecomposition of the q x q Gram X0^H X0 (FP64 sums, FP32
-// Jacobi), sigma_j = sqrt(lambda_j) sorted descending, and the rank rule of
-// Alg. 2 when rank_in == 0: the smallest r whose leading sigma^2 reach b% of
-// the energy of the first floor(min(n, q, C min m_k)/10) (at least 1).
+// Eigendecomposition of the q x q Gram A = X0^H X0 (Alg. 2: sigma_j^2 and the
+// right singular vectors of X0) in two passes, each a parallel cyclic Jacobi
+// in FP32 in one block:
+//   pass 0 : Jacobi on A (rounded to FP32) -> V0.  Its rotations leave errors
+//            of about eps ||A|| in every entry, so the eigenvectors of small
+//            eigenvalues are off by about eps lambda_1 / gap;
+//   refine : B = V0^H A V0 formed in FP64 (k_refine_av, k_refine_vhb), whose
+//            off-diagonal entries are those small errors, held in FP32 with
+//            full relative precision; a second Jacobi (relative threshold
+//            only) on B -> Q, and V = V0 Q.  The second pass's rounding is
+//            relative to the entries it rotates, so every eigenpair comes out
+//            accurate relative to its own eigenvalue and gap (mixed-precision
+//            Jacobi refinement).
+// The refine pass also sorts: sigma_j = sqrt(lambda_j) descending, and the
+// rank rule of Alg. 2 when rank_in == 0: the smallest r whose leading sigma^2
+// reach b% of the energy of the first floor(min(n, q, C min m_k)/10) (at least 1).
 __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int rank_in, int rmax,
-                      double energy_pct, float2 *V, int32_t *order, double *sigma, int32_t *meta,
-                      unsigned int *status, int v_in_smem) {
-    // A (and V when it fits) in shared memory with an odd row pitch, so that
-    // the column updates of the rotations hit distinct banks
+                      double energy_pct, float2 *V, float2 *Q, int32_t *order, double *sigma, int32_t *meta,
+                      unsigned int *status, int v_in_smem, int refine) {
+    // A (and the rotation matrix when it fits) in shared memory with an odd row
+    // pitch, so that the column updates of the rotations hit distinct banks
     extern __shared__ float2 sA[];
     __shared__ float s_c[64], s_s[64];
     __shared__ float2 s_e[64];
     __shared__ int s_cnt;
     __shared__ double s_fro[32];
+    __shared__ double s_scale;
+    __shared__ float s_lam[128];
     const int ld = q | 1;
-    float2 *Vw = v_in_smem ? sA + q * ld : V;
+    float2 *Vw = v_in_smem ? sA + q * ld : (refine ? Q : V);
     const int ldv = v_in_smem ? ld : q;
+    if (threadIdx.x == 0) {   // the refine pass works on B / max diag(B)
+        double mx = 0.0;
+        if (refine)
+            for (int i = 0; i < q; ++i) mx = fmax(mx, gram[2 * (i * q + i)]);
+        s_scale = mx > 0.0 ? mx : 1.0;
+    }
+    __syncthreads();
+    const double isc = refine ? 1.0 / s_scale : 1.0;
     double fro = 0.0;
     for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
         const int a = e / q, b = e - a * q;
-        sA[a * ld + b] = make_float2((float)gram[2 * e], (float)gram[2 * e + 1]);
+        sA[a * ld + b] = make_float2((float)(gram[2 * e] * isc), (float)(gram[2 * e + 1] * isc));
         Vw[a * ldv + b] = make_float2(a == b ? 1.f : 0.f, 0.f);
         fro += gram[2 * e] * gram[2 * e] + gram[2 * e + 1] * gram[2 * e + 1];
     }
@@ -475,29 +497,38 @@ __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int
     __syncthreads();
     fro = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fro += s_fro[w];
-    // a rotation is skipped once |a_pq| <= 1e-6 sqrt(a_pp a_qq) or <= 1e-7 ||A||_F.
-    // FP32 rounding keeps regenerating off-diagonal entries near that floor
-    // (between large and noise-level eigenvalues), so the sweeps rarely all skip;
-    // cyclic Jacobi converges quadratically and reaches the floor within 8
-    // sweeps for these sizes (parity bounds: 1e-4 on sigma and on SD(U0))
-    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 8, (float)(1e-7 * sqrt(fro)), 1e-6f);
-    if (v_in_smem)
-        for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = Vw[(e / q) * ldv + e % q];
-    // diagonal to a compact array (the sort below reads sA[i * q + i])
+    if (!refine) {
+        // a rotation is skipped once |a_pq| <= 1e-6 sqrt(a_pp a_qq) or <= 1e-7
+        // ||A||_F: FP32 rounding keeps regenerating off-diagonal entries near
+        // that floor, which the refine pass removes
+        block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 8, (float)(1e-7 * sqrt(fro)), 1e-6f);
+        if (v_in_smem)
+            for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = Vw[(e / q) * ldv + e % q];
+        return;
+    }
+    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 6, 0.f, 1e-6f);
+    // eigenvalues (diagonal of the rotated B, scaled back), then V <- V0 Q,
+    // formed in the shared A region (A is no longer needed)
+    for (int i = threadIdx.x; i < q; i += blockDim.x) s_lam[i] = sA[i * ld + i].x;
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int i = 0; i < q; ++i) sA[i * q + i] = sA[i * ld + i];
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        const int a = e / q, b = e - a * q;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int m = 0; m < q; ++m) cfma(acc, V[a * q + m], Vw[m * ldv + b]);
+        sA[a * ld + b] = acc;
+    }
     __syncthreads();
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = sA[(e / q) * ld + e % q];
     // eigenvalue order, descending (ties by index): thread i finds its rank
     for (int i = threadIdx.x; i < q; i += blockDim.x) {
-        const float li = sA[i * q + i].x;
+        const float li = s_lam[i];
         int rank = 0;
         for (int j = 0; j < q; ++j) {
-            const float lj = sA[j * q + j].x;
+            const float lj = s_lam[j];
             rank += (lj > li || (lj == li && j < i)) ? 1 : 0;
         }
         order[rank] = i;
-        sigma[rank] = sqrt(li > 0.f ? (double)li : 0.0);
+        sigma[rank] = sqrt(li > 0.f ? (double)li * s_scale : 0.0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -519,6 +550,43 @@ __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int
         meta[MT_RANK] = r;
         if (r > rmax || r > q) atomicOr(status, (unsigned)ST_ZERO_SIGMA);
         else if (!(sigma[r - 1] > 0.0)) atomicOr(status, (unsigned)ST_ZERO_SIGMA);
+    }
+}
+
+// T = A V0 in FP64 (A: the FP64 Gram, (re, im) pairs; V0: FP32 eigenvectors
+// of pass 0): block a forms row a of T.
+__global__ void k_refine_av(const double *__restrict__ gram, const float2 *__restrict__ V, int q, double *T) {
+    const int a = blockIdx.x;
+    for (int b = threadIdx.x; b < q; b += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < q; ++j) {
+            const double ar = gram[2 * (a * q + j)], ai = gram[2 * (a * q + j) + 1];
+            const float2 v = V[j * q + b];
+            re += ar * v.x - ai * v.y;
+            im += ar * v.y + ai * v.x;
+        }
+        T[2 * (a * q + b)] = re;
+        T[2 * (a * q + b) + 1] = im;
+    }
+}
+
+// B = V0^H T in FP64, made exactly Hermitian (the mean of B and B^H): block a
+// forms row a; entries (a, b) and (b, a) are summed in the same order.
+__global__ void k_refine_vhb(const float2 *__restrict__ V, const double *__restrict__ T, int q, double *Bm) {
+    const int a = blockIdx.x;
+    for (int b = threadIdx.x; b < q; b += blockDim.x) {
+        double re = 0.0, im = 0.0, re2 = 0.0, im2 = 0.0;
+        for (int i = 0; i < q; ++i) {
+            const float2 va = V[i * q + a], vb = V[i * q + b];
+            const double tr = T[2 * (i * q + b)], ti = T[2 * (i * q + b) + 1];   // T[i][b]
+            const double ur = T[2 * (i * q + a)], ui = T[2 * (i * q + a) + 1];   // T[i][a]
+            re += va.x * tr + va.y * ti;    // conj(V[i][a]) T[i][b] = B[a][b]
+            im += va.x * ti - va.y * tr;
+            re2 += vb.x * ur + vb.y * ui;   // conj(V[i][b]) T[i][a] = B[b][a]
+            im2 += vb.x * ui - vb.y * ur;
+        }
+        Bm[2 * (a * q + b)] = 0.5 * (re + re2);
+        Bm[2 * (a * q + b) + 1] = 0.5 * (im - im2);
     }
 }
 
@@ -546,9 +614,22 @@ cudaError_t launch_gram_x0(lrccs_ctx *c) {
     const int ld = q | 1;
     const int v_in_smem = (size_t)2 * q * ld * sizeof(float2) + 4096 <= (size_t)c->dev_smem_optin;
     const size_t smem2 = (size_t)(v_in_smem ? 2 : 1) * q * ld * sizeof(float2);
+    double *T = c->d_gram + 2 * (size_t)q * q, *Bm = T + 2 * (size_t)q * q;
     prof_begin(c, KID_EIG);
     k_eig<<<1, 1024, smem2, c->stream>>>(gram, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
-                                        c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem);
+                                        c->d_Q, c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem,
+                                        0);
+    prof_end(c, KID_EIG);
+    prof_begin(c, KID_EIG);
+    k_refine_av<<<q, 128, 0, c->stream>>>(gram, c->d_V, q, T);
+    prof_end(c, KID_EIG);
+    prof_begin(c, KID_EIG);
+    k_refine_vhb<<<q, 128, 0, c->stream>>>(c->d_V, T, q, Bm);
+    prof_end(c, KID_EIG);
+    prof_begin(c, KID_EIG);
+    k_eig<<<1, 1024, smem2, c->stream>>>(Bm, q, c->n, c->nc, c->dims.rank, c->rmax, c->prm.energy_pct, c->d_V,
+                                        c->d_Q, c->d_meta + MT_COUNT, c->d_sigma, c->d_meta, c->d_status, v_in_smem,
+                                        1);
     prof_end(c, KID_EIG);
     return cudaGetLastError();
 }

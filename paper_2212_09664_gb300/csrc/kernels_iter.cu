@@ -368,16 +368,17 @@ typedef void (*row_w_t)(float2 *, const float2 *, const int32_t *, const int32_t
 static const row_gram_t kRowGram[RMAXC] = RANK_TABLE(k_row_gram);
 static const row_w_t kRowW[RMAXC] = RANK_TABLE(k_row_w);
 
-// One launcher per iteration kernel, at the context's current rank c->r.
-static cudaError_t launch_fwd_cols(lrccs_ctx *c) {
-    const int r = c->r, nx = c->nx, ny = c->ny;
+// One launcher per iteration kernel, at the context's current rank c->r (the
+// _on / _to forms take the source or destination and the column count).
+cudaError_t launch_fwd_cols_on(lrccs_ctx *c, const float2 *src, int r) {
+    const int nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
     const int tx = fwd_tile_x(r, nx);
     const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
     dim3 grid(nx / tx, c->nc);
     DISPATCH_P(c->py, {
         prof_begin(c, KID_FWD_COLS);
-        k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(c->d_U, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
+        k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(src, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
                                                        c->d_twy, sy);
         prof_end(c, KID_FWD_COLS);
     });
@@ -416,9 +417,9 @@ static void launch_row_w(lrccs_ctx *c) {
     prof_end(c, KID_ROW_W);
 }
 
-// coil-summed inverse transform into the U+ buffer (free during iterations)
-static cudaError_t launch_adj_cols(lrccs_ctx *c) {
-    const int r = c->r, nx = c->nx, ny = c->ny;
+// coil-summed inverse transform into dst (n x r)
+cudaError_t launch_adj_cols_to(lrccs_ctx *c, float2 *dst, int r) {
+    const int nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
     const size_t smem = ((size_t)4 * ny * r + 5 * (size_t)ny) * sizeof(float2);
     const int cg = adj_cluster(c->nc);
@@ -440,14 +441,18 @@ static cudaError_t launch_adj_cols(lrccs_ctx *c) {
         prof_begin(c, KID_ADJ_COLS);
         if (small)
             el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 8>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
-                                    (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
+                                    (const uint8_t *)c->d_rowused, dst, nx, r, c->nc, (const float2 *)c->d_twy, sy);
         else
             el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 16>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
-                                    (const uint8_t *)c->d_rowused, c->d_Up, nx, r, c->nc, (const float2 *)c->d_twy, sy);
+                                    (const uint8_t *)c->d_rowused, dst, nx, r, c->nc, (const float2 *)c->d_twy, sy);
         prof_end(c, KID_ADJ_COLS);
     });
     return el;
 }
+
+static cudaError_t launch_fwd_cols(lrccs_ctx *c) { return launch_fwd_cols_on(c, c->d_U, c->r); }
+// the iteration's coil-summed inverse transform goes to the U+ buffer (free during iterations)
+static cudaError_t launch_adj_cols(lrccs_ctx *c) { return launch_adj_cols_to(c, c->d_Up, c->r); }
 
 cudaError_t launch_iteration(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
@@ -470,6 +475,18 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     if (e != cudaSuccess) return e;
     // F: gradient, GD step and CholeskyQR2 (one cooperative launch)
     return launch_gdqr(c, 1);
+}
+
+// The B-step alone at the current U (U^H Z already in the totals): forward
+// transforms, Grams and the per-frame solves.
+cudaError_t launch_bstep(lrccs_ctx *c) {
+    if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    cudaError_t el = launch_fwd_cols(c);
+    if (el != cudaSuccess) return el;
+    if (c->general) return launch_iteration_general_front(c);
+    el = launch_row_gram(c);
+    if (el != cudaSuccess) return el;
+    return launch_solve(c);
 }
 
 // The normal operator of the stacked A = [A_1; ...; A_q] with B = 1 (q x 1):

@@ -66,6 +66,9 @@ _sig = {
     "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
+    "lrccs_mec1": (_st, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "lrccs_mec2": (_st, [_vp, C.c_int32, C.c_double, C.c_double, _vp, _vp, _vp, C.POINTER(C.c_int32)]),
+    "lrccs_online_frames": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp]),
     "lrccs_destroy": (None, [_vp]),
     "lrccs_last_error": (C.c_char_p, [_vp]),
     "lrccs_status_string": (C.c_char_p, [_st]),
@@ -232,6 +235,23 @@ def lrccs_test_wait_timeout(ctx, enable: bool = True):
     _check(ctx, _lib.lrccs_test_wait_timeout(ctx, 1 if enable else 0))
 
 
+def lrccs_mec1(ctx, iters: int = 3, zbar=None, E=None, X=None):
+    _check(ctx, _lib.lrccs_mec1(ctx, int(iters), _ptr(zbar), _ptr(E), _ptr(X)))
+
+
+def lrccs_mec2(ctx, max_iter: int = 10, rel_change: float = 0.0025, omega_frac: float = 0.001, zbar=None, E=None,
+               X=None) -> int:
+    it = C.c_int32(0)
+    _check(ctx, _lib.lrccs_mec2(ctx, int(max_iter), float(rel_change), float(omega_frac), _ptr(zbar), _ptr(E),
+                                _ptr(X), C.byref(it)))
+    return it.value
+
+
+def lrccs_online_frames(ctx, y, frame_ptr, mask, smaps, zbar, mec_iters: int = 3, X=None, B=None):
+    _check(ctx, _lib.lrccs_online_frames(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps), _ptr(zbar),
+                                         int(mec_iters), _ptr(X), _ptr(B)))
+
+
 def lrccs_last_error(ctx=None) -> str:
     return (_lib.lrccs_last_error(ctx) or b"").decode()
 
@@ -287,6 +307,32 @@ class Solver:
         """One later mini-batch of Alg. 4 (warm start, t_max iterations).  X: optional
         (q, n) complex64 output, row k = x_k.  Returns the info dict when info=True."""
         return lrccs_track_minibatch(self.ctx, y, frame_ptr, mask, smaps, t_max, reset_eta, X, info)
+
+    def mec1(self, iters=3, zbar=None):
+        """Alg. 3 MEC-1 after the iterations: returns (E, X), each (q, n), row k
+        = e_k and x_k = zbar + U_{t-1} b_k + e_k."""
+        t = self._torch
+        E = t.empty((self.q, self.n), dtype=t.complex64, device="cuda")
+        X = t.empty_like(E)
+        lrccs_mec1(self.ctx, iters, zbar, E, X)
+        return E, X
+
+    def mec2(self, max_iter=10, rel_change=0.0025, omega_frac=0.001, zbar=None):
+        """Alg. 3 MEC-2 (ISTA, temporal DFT): returns (E, X, ISTA updates)."""
+        t = self._torch
+        E = t.empty((self.q, self.n), dtype=t.complex64, device="cuda")
+        X = t.empty_like(E)
+        it = lrccs_mec2(self.ctx, max_iter, rel_change, omega_frac, zbar, E, X)
+        return E, X, it
+
+    def online(self, y, frame_ptr, mask, smaps, zbar, mec_iters=3):
+        """Alg. 5 on this context's q frames with the subspace set by set_subspace:
+        returns (X (q, n), B (q, r) with row k = b_k)."""
+        t = self._torch
+        X = t.empty((self.q, self.n), dtype=t.complex64, device="cuda")
+        B = t.empty((self.q, self.r), dtype=t.complex64, device="cuda")
+        lrccs_online_frames(self.ctx, y, frame_ptr, mask, smaps, zbar, mec_iters, X, B)
+        return X, B
 
     def get_state(self) -> bytes:
         return lrccs_get_state(self.ctx)
