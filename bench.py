@@ -437,6 +437,127 @@ def mean_step_leg(p, dev, stream, reps=10):
                          "transforms), residual pass")
 
 
+RADIAL_WORKLOAD = "radial256_q64_c20_r12"
+
+
+def radial_leg(dev, stream, steps=5, warmup=3):
+    """The precision-form workload's shape (256 x 256, q = 64, 20 coils, r = 12,
+    16 golden-angle pseudo-radial spokes per frame) solved by the FP32 FFT path
+    (general 2D masks: x transforms, per-point Grams and W): init + 50
+    graph-replayed iterations per solve, inputs resident, CUDA events on the
+    library stream, the L2 flushed between solves.  Also the per-kernel event
+    times of one solve and the iteration's algorithmic bytes against HBM."""
+    import numpy as np
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs, synth
+
+    p = synth.make_problem(RADIAL_WORKLOAD)
+    with torch.cuda.stream(stream):
+        y, fp, mask, sm = (torch.from_numpy(a).to(dev) for a in (p.y, p.frame_ptr, p.mask, p.smaps))
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+
+    def solve(mid=None):
+        lrccs.lrccs_init(s.ctx, y, fp, mask, sm)
+        if mid is not None:
+            mid.record(stream)
+        lrccs.lrccs_iterate(s.ctx, T_ITER)
+
+    lrccs.lrccs_profile(s.ctx, "*")
+    for _ in range(warmup):
+        solve()
+    stats = lrccs.lrccs_profile_read(s.ctx)
+    lrccs.lrccs_profile(s.ctx, None)
+    solve()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for a, m, b in ev:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a.record(stream)
+        solve(m)
+        b.record(stream)
+    torch.cuda.synchronize()
+    tot = sum(a.elapsed_time(b) for a, _, b in ev)
+    init = sum(a.elapsed_time(m) for a, m, _ in ev)
+    it_ms = (tot - init) / steps / T_ITER
+    nu = int(p.mask.any(0).sum())
+    n, q, C, r = p.n, p.q, p.nc, p.rank
+    # algorithmic bytes of one general-mask iteration (complex64 = 8 B): U, maps
+    # and the rows of T (fwd_cols); T in, FU out (fwd_rows); FU (Grams); FU in
+    # and out (W); FU in, T out (adj_rows); T, maps in, Gk out (adj_cols); k_gdqr
+    rows = int(p.mask.reshape(q, p.ny, p.nx).any(2).any(0).sum())
+    t_rows = C * r * rows * p.nx
+    it_bytes = 8 * ((n * r + C * n + t_rows) + (t_rows + C * r * nu) + C * r * nu + 2 * C * r * nu
+                    + (C * r * nu + t_rows) + (t_rows + C * n + n * r) + (5 * n * r + n * q))
+    peak, peak_kind = peaks()
+    per_kernel = {d["name"]: d["ms"] / d["timed"] * 1e3 for d in stats if d["timed"] > 0 and d["launches"] > 0}
+    s.close()
+    return dict(workload=RADIAL_WORKLOAD, ny=p.ny, nx=p.nx, q=q, coils=C, rank=r, spokes=16, union_points=nu,
+                solves=steps, value=q * T_ITER * steps / (tot / 1e3), unit=UNIT,
+                iterations_only=q * T_ITER * steps / ((tot - init) / 1e3), ms_per_iteration=it_ms,
+                init_ms_per_solve=init / steps, iteration_alg_bytes=it_bytes,
+                iteration_hbm_frac=it_bytes / (it_ms / 1e3) / 1e9 / peak, peak_source=peak_kind,
+                kernel_us_per_launch=per_kernel,
+                parity="per-iterate NRMSE against the FP64 oracle is a GPU test (init + 2 iterates at this size); "
+                       "the oracle's 50-iteration solve at this size takes too long for the bench")
+
+
+def alg1_leg(p, dev, stream, reps=5):
+    """Full Alg. 1 on the workload through the C ABI: the mean step
+    (lrccs_mean_step, CGLS tol 1e-3, <= 10 iterations, then y~), Alg. 2 on y~
+    (lrccs_init + lrccs_iterate(50)) and MEC: altGDmin-MRI1 with MEC-1 (3 CGLS
+    iterations per frame, lrccs_mec1) and altGDmin-MRI2 with MEC-2 (ISTA on the
+    temporal DFT, lrccs_mec2), each writing X = zbar + U B + E.  CUDA events
+    on the library stream; the mean step and MEC-2 wait for their stopping tests."""
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs
+
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    with torch.cuda.stream(stream):
+        y, fp, mask, sm = (torch.from_numpy(a).to(dev) for a in (p.y, p.frame_ptr, p.mask, p.smaps))
+        zbar = torch.empty((p.n,), dtype=torch.complex64, device=dev)
+        ytil = torch.empty_like(y)
+        E = torch.empty((p.q, p.n), dtype=torch.complex64, device=dev)
+        X = torch.empty_like(E)
+    out = {}
+    for name in ("mri1", "mri2"):
+        marks = []
+
+        def run():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            lrccs.lrccs_mean_step(s.ctx, y, fp, mask, sm, zbar, ytil)
+            ev[1].record(stream)
+            lrccs.lrccs_init(s.ctx, ytil, fp, mask, sm)
+            lrccs.lrccs_iterate(s.ctx, T_ITER)
+            ev[2].record(stream)
+            it = 3
+            if name == "mri1":
+                lrccs.lrccs_mec1(s.ctx, 3, zbar, E, X)
+            else:
+                it = lrccs.lrccs_mec2(s.ctx, 10, 0.0025, 0.001, zbar, E, X)
+            ev[3].record(stream)
+            return ev, it
+
+        for _ in range(2):
+            run()
+        its = 0
+        for _ in range(reps):
+            ev, its = run()
+            marks.append(ev)
+        torch.cuda.synchronize()
+        parts = [[a.elapsed_time(b) for a, b in zip(ev[:-1], ev[1:])] for ev in marks]
+        mean = [sum(x[i] for x in parts) / reps for i in range(3)]
+        out[name] = dict(ms_total=sum(mean), ms_mean_step=mean[0], ms_altgdmin=mean[1], ms_mec=mean[2],
+                         mec_iterations=its, mec="MEC-1 (3 CGLS per frame)" if name == "mri1" else
+                         "MEC-2 (ISTA, temporal DFT, <= 10 steps)")
+    s.close()
+    return out
+
+
 def serving_parity(part, U_prev, eta, X_gpu):
     """NRMSE of one tracked mini-batch's images against the FP64 oracle run from the
     same warm start U^(j-1) and step size (part of the CPU-baseline leg)."""
@@ -458,6 +579,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the mini-batch tracking latency leg")
     ap.add_argument("--no-comparators", action="store_true", help="skip the cuFFT / cuBLAS comparator timings")
+    ap.add_argument("--no-radial", action="store_true", help="skip the 256 x 256 pseudo-radial workload leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -612,6 +734,15 @@ def main():
             line["mean_step"] = mean_step_leg(p, dev, stream)
         except Exception as e:
             line["mean_step"] = dict(error="%s: %s" % (type(e).__name__, e))
+        try:
+            line["alg1"] = alg1_leg(p, dev, stream)
+        except Exception as e:
+            line["alg1"] = dict(error="%s: %s" % (type(e).__name__, e))
+    if ws == 1 and not args.no_radial:
+        try:
+            line["radial_fp32"] = radial_leg(dev, stream)
+        except Exception as e:
+            line["radial_fp32"] = dict(error="%s: %s" % (type(e).__name__, e))
     sv_check = None
     if ws == 1 and not args.no_serving:
         try:

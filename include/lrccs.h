@@ -63,12 +63,22 @@ typedef enum lrccs_status {
     LRCCS_E_UNSUPPORTED = 8       /* valid input outside this build's scope (see above) */
 } lrccs_status;
 
+/* Arithmetic of the transforms.  This build has the FP32 FFT path only; the
+ * tensor-core DFT-as-GEMM forms are reserved values that lrccs_create refuses
+ * with LRCCS_E_UNSUPPORTED. */
+typedef enum lrccs_precision {
+    LRCCS_PREC_FP32_FFT = 0,      /* FP32 fast Fourier transforms, FP32 accumulation */
+    LRCCS_PREC_BF16X3_GEMM = 1,   /* (not built) DFT as GEMM, 3-term BF16 split */
+    LRCCS_PREC_FP16S_GEMM = 2     /* (not built) DFT as GEMM, FP16 with per-tile scaling */
+} lrccs_precision;
+
 typedef struct lrccs_dims {
     int32_t ny, nx;     /* image size */
     int32_t q;          /* number of frames */
     int32_t ncoil;      /* number of coils C */
     int32_t rank;       /* r > 0 fixes the rank; 0 selects it by the energy rule of Alg. 2 */
     int32_t rank_max;   /* buffer capacity for the rank (>= rank, <= 16); 0 -> 16 */
+    int32_t precision;  /* lrccs_precision */
 } lrccs_dims;
 
 typedef struct lrccs_params {
@@ -78,6 +88,8 @@ typedef struct lrccs_params {
     double eps_exit;       /* 0.01 : exit when SD(U_{t-1}, U_t)/sqrt(r) < eps_exit (Alg. 2) */
     int32_t t_max;         /* 70   : iteration cap used by callers that solve to completion */
     int32_t exit_enabled;  /* 1: lrccs_iterate stops at the exit test (one host sync per iteration) */
+    double admit_reserve_bytes;  /* 256 MiB: device memory that must stay free after lrccs_create's
+                                    buffers, or the context is not admitted (LRCCS_E_ADMISSION) */
 } lrccs_params;
 
 typedef struct lrccs_iter_info {
@@ -88,17 +100,28 @@ typedef struct lrccs_iter_info {
     double gnorm;       /* ||grad||_2 of the first iteration (defines eta) */
 } lrccs_iter_info;
 
-/* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off). */
+/* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off) and a
+ * 256 MiB admission reserve. */
 void lrccs_default_params(lrccs_params *p);
 
 /* Create a context for one problem size on the current CUDA device.  The rank
  * may exceed q (a context that tracks mini-batches of fewer than r frames);
  * lrccs_init then refuses the fixed rank.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  Allocates every
- * device buffer the solve needs.  Errors: LRCCS_E_INVALID (dims outside scope),
- * LRCCS_E_NOMEM, LRCCS_E_CUDA. */
+ * device buffer the solve needs, after an admission check: the total
+ * (lrccs_context_bytes) plus params->admit_reserve_bytes must not exceed the
+ * device's free memory (cudaMemGetInfo), else nothing is allocated and the call
+ * returns LRCCS_E_ADMISSION; a serving loop retries once other contexts are
+ * destroyed.  Errors: LRCCS_E_INVALID (dims outside scope), LRCCS_E_UNSUPPORTED
+ * (a precision that is not built), LRCCS_E_ADMISSION, LRCCS_E_NOMEM, LRCCS_E_CUDA. */
 lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params,
                           void *cuda_stream, lrccs_ctx **out);
+
+/* Device bytes lrccs_create would allocate for dims (each buffer rounded up to
+ * 256 bytes).  Not included: the general-mask and MEC work space, allocated by
+ * the first call that needs them (see lrccs_init, lrccs_mec1).  Allocates
+ * nothing.  Errors: LRCCS_E_INVALID, LRCCS_E_UNSUPPORTED. */
+lrccs_status lrccs_context_bytes(const lrccs_dims *dims, size_t *bytes);
 
 /* Spectral initialisation (Alg. 2, initialisation) from the measurements.
  *   d_y        : complex64, ragged (see conventions), C * fp[q] entries
@@ -292,6 +315,32 @@ lrccs_status lrccs_set_subspace(lrccs_ctx *ctx, const void *d_U, int32_t rank, d
 lrccs_status lrccs_track_minibatch(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
                                    const uint8_t *d_mask, const void *d_smaps, int32_t t_max,
                                    int32_t reset_eta, void *d_X, lrccs_iter_info *info);
+
+/* Asynchronous form of lrccs_track_minibatch for serving loops (Alg. 4 as a
+ * request loop).  The call only enqueues the request on the context's host
+ * worker thread (started by the first such call) and returns at once with a
+ * ticket; the worker runs lrccs_track_minibatch (including its wait for the
+ * mask compaction) and queues the GPU work on the context's stream, so one
+ * submitting thread can keep many contexts busy.  Requests of one context run
+ * in submission order.  The inputs (d_y, d_frame_ptr, d_mask, d_smaps) must
+ * stay valid and unchanged, and d_X untouched, until the ticket completes;
+ * while any ticket of the context is pending only lrccs_ticket_query,
+ * lrccs_ticket_wait and lrccs_track_minibatch_async may be called on it.
+ * Errors: LRCCS_E_INVALID (null pointer, t_max < 1), LRCCS_E_CUDA. */
+typedef struct lrccs_ticket { uint64_t id; } lrccs_ticket;
+lrccs_status lrccs_track_minibatch_async(lrccs_ctx *ctx, const void *d_y, const int64_t *d_frame_ptr,
+                                         const uint8_t *d_mask, const void *d_smaps, int32_t t_max,
+                                         int32_t reset_eta, void *d_X, lrccs_ticket *ticket);
+/* *done = 1 once the request has run and its GPU work has finished (0 while
+ * pending).  Does not block.  Returns the request's status once it has run
+ * (a host-side failure of lrccs_track_minibatch), LRCCS_OK while pending.
+ * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (unknown or expired ticket: results of
+ * the last 256 requests are kept). */
+lrccs_status lrccs_ticket_query(lrccs_ctx *ctx, const lrccs_ticket *ticket, int32_t *done);
+/* Block until the request has run and its GPU work has finished; returns its
+ * status, including device-side failures (non-SPD systems, timeouts) recorded
+ * by its kernels. */
+lrccs_status lrccs_ticket_wait(lrccs_ctx *ctx, const lrccs_ticket *ticket);
 
 /* Checkpoint and resume of the solver state that later iterations depend on:
  * ny, nx, the rank r, the iteration count t, the step size eta (and whether it

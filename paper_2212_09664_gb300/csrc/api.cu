@@ -6,12 +6,17 @@
 
 #include <new>
 #include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 
 #include "internal.h"
 #include "lrccs.h"
 
 static std::string g_create_err;
+static std::mutex g_err_mutex;   // the async worker and the caller's thread may both report errors
 
 void set_err(lrccs_ctx *c, const char *fmt, ...) {
     char buf[512];
@@ -19,6 +24,7 @@ void set_err(lrccs_ctx *c, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
+    std::lock_guard<std::mutex> lock(g_err_mutex);
     if (c) c->err = buf;
     else g_create_err = buf;
 }
@@ -45,6 +51,7 @@ extern "C" void lrccs_default_params(lrccs_params *p) {
     p->eps_exit = 0.01;
     p->t_max = 70;
     p->exit_enabled = 0;
+    p->admit_reserve_bytes = 268435456.0;
 }
 
 extern "C" const char *lrccs_status_string(lrccs_status s) {
@@ -92,13 +99,13 @@ static bool dalloc(lrccs_ctx *c, T **p, size_t count) {
 
 static bool pow_ok(int v) { return v >= 32 && v <= 256 && v % 32 == 0; }
 
-extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params, void *cuda_stream,
-                                     lrccs_ctx **out) {
-    if (!dims || !out) {
+static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *params, void *cuda_stream,
+                                lrccs_ctx **out, size_t *out_bytes_only) {
+    if (!dims || (!out && !out_bytes_only)) {
         set_err(nullptr, "lrccs_create: dims and out must be non-null");
         return LRCCS_E_INVALID;
     }
-    *out = nullptr;
+    if (out) *out = nullptr;
     const lrccs_dims d = *dims;
     int rmax = d.rank_max > 0 ? d.rank_max : (d.rank > 0 ? d.rank : 16);
     if (!pow_ok(d.ny) || !pow_ok(d.nx) || d.q < 1 || d.q > 128 || d.ncoil < 1 || d.ncoil > 64 || d.rank < 0 ||
@@ -108,12 +115,17 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
                 "ncoil in [1,64]; 0 <= rank <= rank_max <= 16)");
         return LRCCS_E_INVALID;
     }
+    if (d.precision != LRCCS_PREC_FP32_FFT) {
+        set_err(nullptr, "lrccs_create: precision %d is not built (only LRCCS_PREC_FP32_FFT)", d.precision);
+        return LRCCS_E_UNSUPPORTED;
+    }
     lrccs_ctx *c = new (std::nothrow) lrccs_ctx();
     if (!c) return LRCCS_E_NOMEM;
     c->dims = d;
     if (params) c->prm = *params;
     else lrccs_default_params(&c->prm);
     c->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
     c->ny = d.ny;
     c->nx = d.nx;
     c->n = d.ny * d.nx;
@@ -142,25 +154,65 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     if (gcap < 1024) gcap = 1024;
     c->gpart_cap = gcap;
     c->T_cap = (size_t)nc * n * rmax;
-    bool ok = dalloc(c, &c->d_twy, ny) && dalloc(c, &c->d_twx, c->nx) && dalloc(c, &c->d_smaps, (size_t)nc * n) &&
-              dalloc(c, &c->d_rowcnt, (size_t)q * ny) && dalloc(c, &c->d_rowidx, (size_t)q * ny) &&
-              dalloc(c, &c->d_framerows, (size_t)q * ny) && dalloc(c, &c->d_lineptr, (size_t)q + 1) &&
-              dalloc(c, &c->d_rfptr, (size_t)ny + 1) && dalloc(c, &c->d_rflist, (size_t)q * ny) &&
-              dalloc(c, &c->d_usedrows, (size_t)ny) && dalloc(c, &c->d_rowused, (size_t)ny) &&
-              dalloc(c, &c->d_idx, (size_t)q * n) && dalloc(c, &c->d_meta, (size_t)MT_COUNT + q) &&
-              dalloc(c, &c->d_status, 1) && dalloc(c, &c->d_counters, CNT_COUNT) &&
-              dalloc(c, &c->d_scal, SC_COUNT) && dalloc(c, &c->d_Z, (size_t)n * q) &&
-              dalloc(c, &c->d_X0, (size_t)n * q) && dalloc(c, &c->d_T, c->T_cap) &&
-              dalloc(c, &c->d_U, (size_t)n * rmax) && dalloc(c, &c->d_Uprev, (size_t)n * rmax) &&
-              dalloc(c, &c->d_Up, (size_t)n * rmax) && dalloc(c, &c->d_G, (size_t)n * rmax) &&
-              dalloc(c, &c->d_B, (size_t)q * rmax) && dalloc(c, &c->d_P, (size_t)ny * npm) &&
-              dalloc(c, &c->d_gpart, gcap) && dalloc(c, &c->d_tot, gd_len) &&
-              dalloc(c, &c->d_sigma, (size_t)q) && dalloc(c, &c->d_gram, (size_t)6 * q * q) &&
-              dalloc(c, &c->d_V, (size_t)q * q) && dalloc(c, &c->d_Q, (size_t)q * q) &&
-              dalloc(c, &c->d_framek, (size_t)q * ny) &&
-              dalloc(c, &c->d_mks, (size_t)q) && dalloc(c, &c->d_fpk, (size_t)q + 1) &&
-              dalloc(c, &c->d_rowoff, (size_t)q * ny) && dalloc(c, &c->d_maskc, (size_t)q * n) &&
-              dalloc(c, &c->d_twq, (size_t)q);
+    // every buffer of the context, as (pointer, bytes); the total is checked
+    // against the free device memory before anything is allocated
+    const size_t F2 = sizeof(float2), I4 = sizeof(int32_t), D8 = sizeof(double);
+    const struct { void **p; size_t bytes; } plan[] = {
+        {(void **)&c->d_twy, ny * F2}, {(void **)&c->d_twx, c->nx * F2}, {(void **)&c->d_smaps, (size_t)nc * n * F2},
+        {(void **)&c->d_rowcnt, (size_t)q * ny * I4}, {(void **)&c->d_rowidx, (size_t)q * ny * I4},
+        {(void **)&c->d_framerows, (size_t)q * ny * I4}, {(void **)&c->d_lineptr, ((size_t)q + 1) * I4},
+        {(void **)&c->d_rfptr, ((size_t)ny + 1) * I4}, {(void **)&c->d_rflist, (size_t)q * ny * I4},
+        {(void **)&c->d_usedrows, (size_t)ny * I4}, {(void **)&c->d_rowused, (size_t)ny},
+        {(void **)&c->d_idx, (size_t)q * n * I4}, {(void **)&c->d_meta, ((size_t)MT_COUNT + q) * I4},
+        {(void **)&c->d_status, sizeof(unsigned)}, {(void **)&c->d_counters, CNT_COUNT * sizeof(unsigned)},
+        {(void **)&c->d_scal, SC_COUNT * D8}, {(void **)&c->d_Z, (size_t)n * q * F2},
+        {(void **)&c->d_X0, (size_t)n * q * F2}, {(void **)&c->d_T, c->T_cap * F2},
+        {(void **)&c->d_U, (size_t)n * rmax * F2}, {(void **)&c->d_Uprev, (size_t)n * rmax * F2},
+        {(void **)&c->d_Up, (size_t)n * rmax * F2}, {(void **)&c->d_G, (size_t)n * rmax * F2},
+        {(void **)&c->d_B, (size_t)q * rmax * F2}, {(void **)&c->d_P, (size_t)ny * npm * F2},
+        {(void **)&c->d_gpart, gcap * F2}, {(void **)&c->d_tot, gd_len * sizeof(double2)},
+        {(void **)&c->d_sigma, (size_t)q * D8}, {(void **)&c->d_gram, (size_t)6 * q * q * D8},
+        {(void **)&c->d_V, (size_t)q * q * F2}, {(void **)&c->d_Q, (size_t)q * q * F2},
+        {(void **)&c->d_framek, (size_t)q * ny * I4}, {(void **)&c->d_mks, (size_t)q * I4},
+        {(void **)&c->d_fpk, ((size_t)q + 1) * I4}, {(void **)&c->d_rowoff, (size_t)q * ny * I4},
+        {(void **)&c->d_maskc, (size_t)q * n}, {(void **)&c->d_twq, (size_t)q * F2},
+    };
+    size_t need = 0;
+    for (const auto &it : plan) need += (it.bytes + 255) & ~(size_t)255;
+    c->create_bytes = need;
+    if (out_bytes_only) {
+        *out_bytes_only = need;
+        delete c;
+        return LRCCS_OK;
+    }
+    // admission: the buffers must fit the free device memory with the reserve left over
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(nullptr, "lrccs_create: cudaMemGetInfo failed");
+        delete c;
+        return LRCCS_E_CUDA;
+    }
+    const double reserve = c->prm.admit_reserve_bytes > 0.0 ? c->prm.admit_reserve_bytes : 0.0;
+    if ((double)need + reserve > (double)fr) {
+        set_err(nullptr, "lrccs_create: admission refused: the context needs %zu bytes and %.0f must stay free, "
+                         "but only %zu bytes of device memory are free", need, reserve, fr);
+        delete c;
+        return LRCCS_E_ADMISSION;
+    }
+    bool ok = true;
+    for (const auto &it : plan) {
+        *it.p = nullptr;
+        if (ok) {
+            cudaError_t e = cudaMalloc(it.p, it.bytes ? it.bytes : 1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_err(c, "cudaMalloc(%zu bytes) failed: %s", it.bytes, cudaGetErrorString(e));
+                *it.p = nullptr;
+                ok = false;
+            }
+        }
+    }
     if (!ok) {
         g_create_err = c->err;
         free_all(c);
@@ -194,10 +246,30 @@ extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params 
     return LRCCS_OK;
 }
 
+extern "C" lrccs_status lrccs_create(const lrccs_dims *dims, const lrccs_params *params, void *cuda_stream,
+                                     lrccs_ctx **out) {
+    if (!out) {
+        set_err(nullptr, "lrccs_create: dims and out must be non-null");
+        return LRCCS_E_INVALID;
+    }
+    return create_impl(dims, params, cuda_stream, out, nullptr);
+}
+
+extern "C" lrccs_status lrccs_context_bytes(const lrccs_dims *dims, size_t *bytes) {
+    if (!bytes) {
+        set_err(nullptr, "lrccs_context_bytes: bytes must be non-null");
+        return LRCCS_E_INVALID;
+    }
+    return create_impl(dims, nullptr, nullptr, nullptr, bytes);
+}
+
 static void drop_iter_graph(lrccs_ctx *c);
+
+static void stop_worker(lrccs_ctx *c);
 
 extern "C" void lrccs_destroy(lrccs_ctx *c) {
     if (!c) return;
+    stop_worker(c);
     cudaStreamSynchronize(c->stream);
     for (const prof_rec &r : c->pending) {
         if (r.graph_owned) continue;   // owned by the graph, released below
@@ -783,6 +855,218 @@ extern "C" lrccs_status lrccs_online_frames(lrccs_ctx *c, const void *d_y, const
     if (d_B) CK(cudaMemcpyAsync(d_B, c->d_B, (size_t)c->q * c->r * sizeof(float2), cudaMemcpyDeviceToDevice,
                                 c->stream));
     return sync_status(c);
+}
+
+// ---------------------------------------------------------------- asynchronous tracking requests
+
+#define ASYNC_SLOTS 256   // results (status, event, device status word) of the last 256 requests
+
+struct track_req {
+    uint64_t id;
+    const void *y;
+    const int64_t *fp;
+    const uint8_t *mask;
+    const void *smaps;
+    int t_max, reset_eta;
+    void *X;
+};
+
+struct async_worker {
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_req, cv_done;
+    std::deque<track_req> queue;
+    bool stop = false;
+    uint64_t next_id = 1, done_id = 0;    // requests run in id order
+    uint64_t slot_id[ASYNC_SLOTS] = {};
+    lrccs_status slot_st[ASYNC_SLOTS] = {};
+    cudaEvent_t slot_ev[ASYNC_SLOTS] = {};
+    unsigned *slot_dev_status = nullptr;  // pinned host words, one per slot
+};
+
+static void worker_main(lrccs_ctx *c) {
+    async_worker *w = c->worker;
+    cudaSetDevice(c->device);
+    for (;;) {
+        track_req r;
+        {
+            std::unique_lock<std::mutex> lock(w->mu);
+            w->cv_req.wait(lock, [&] { return w->stop || !w->queue.empty(); });
+            if (w->queue.empty()) return;   // stop requested and nothing left
+            r = w->queue.front();
+            w->queue.pop_front();
+        }
+        const int sl = (int)(r.id % ASYNC_SLOTS);
+        lrccs_status st =
+            lrccs_track_minibatch(c, r.y, r.fp, r.mask, r.smaps, r.t_max, r.reset_eta, r.X, nullptr);
+        if (st == LRCCS_OK) {
+            // the request's device status word, read back behind its kernels
+            if (cudaMemcpyAsync(w->slot_dev_status + sl, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaEventRecord(w->slot_ev[sl], c->stream) != cudaSuccess) {
+                cudaGetLastError();
+                st = LRCCS_E_CUDA;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lock(w->mu);
+            w->slot_id[sl] = r.id;
+            w->slot_st[sl] = st;
+            w->done_id = r.id;
+        }
+        w->cv_done.notify_all();
+    }
+}
+
+static lrccs_status start_worker(lrccs_ctx *c) {
+    if (c->worker) return LRCCS_OK;
+    async_worker *w = new (std::nothrow) async_worker();
+    if (!w) return LRCCS_E_NOMEM;
+    if (cudaHostAlloc((void **)&w->slot_dev_status, ASYNC_SLOTS * sizeof(unsigned), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        delete w;
+        set_err(c, "lrccs_track_minibatch_async: cudaHostAlloc failed");
+        return LRCCS_E_CUDA;
+    }
+    for (int i = 0; i < ASYNC_SLOTS; ++i) {
+        if (cudaEventCreateWithFlags(&w->slot_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < i; ++j) cudaEventDestroy(w->slot_ev[j]);
+            cudaFreeHost(w->slot_dev_status);
+            delete w;
+            set_err(c, "lrccs_track_minibatch_async: cudaEventCreate failed");
+            return LRCCS_E_CUDA;
+        }
+    }
+    c->worker = w;
+    w->th = std::thread(worker_main, c);
+    return LRCCS_OK;
+}
+
+static void stop_worker(lrccs_ctx *c) {
+    async_worker *w = c->worker;
+    if (!w) return;
+    {
+        std::lock_guard<std::mutex> lock(w->mu);
+        w->stop = true;
+    }
+    w->cv_req.notify_all();
+    if (w->th.joinable()) w->th.join();
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < ASYNC_SLOTS; ++i) cudaEventDestroy(w->slot_ev[i]);
+    cudaFreeHost(w->slot_dev_status);
+    delete w;
+    c->worker = nullptr;
+}
+
+extern "C" lrccs_status lrccs_track_minibatch_async(lrccs_ctx *c, const void *d_y, const int64_t *d_frame_ptr,
+                                                    const uint8_t *d_mask, const void *d_smaps, int32_t t_max,
+                                                    int32_t reset_eta, void *d_X, lrccs_ticket *ticket) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!d_y || !d_frame_ptr || !d_mask || !d_smaps || !ticket || t_max < 1) {
+        set_err(c, "lrccs_track_minibatch_async: null pointer or t_max < 1");
+        return LRCCS_E_INVALID;
+    }
+    lrccs_status s = start_worker(c);
+    if (s != LRCCS_OK) return s;
+    async_worker *w = c->worker;
+    {
+        std::lock_guard<std::mutex> lock(w->mu);
+        track_req r;
+        r.id = w->next_id++;
+        r.y = d_y;
+        r.fp = d_frame_ptr;
+        r.mask = d_mask;
+        r.smaps = d_smaps;
+        r.t_max = t_max;
+        r.reset_eta = reset_eta;
+        r.X = d_X;
+        w->queue.push_back(r);
+        ticket->id = r.id;
+    }
+    w->cv_req.notify_one();
+    return LRCCS_OK;
+}
+
+// The slot of a ticket that has run, or -1 (expired / unknown); w->mu held.
+static int ticket_slot(async_worker *w, uint64_t id) {
+    const int sl = (int)(id % ASYNC_SLOTS);
+    return (id >= 1 && w->slot_id[sl] == id) ? sl : -1;
+}
+
+extern "C" lrccs_status lrccs_ticket_query(lrccs_ctx *c, const lrccs_ticket *t, int32_t *done) {
+    if (!c || !t || !done) return LRCCS_E_INVALID;
+    async_worker *w = c->worker;
+    if (!w || t->id < 1) {
+        set_err(c, "lrccs_ticket_query: unknown ticket");
+        return LRCCS_E_STATE;
+    }
+    std::unique_lock<std::mutex> lock(w->mu);
+    if (t->id >= w->next_id) {
+        set_err(c, "lrccs_ticket_query: unknown ticket");
+        return LRCCS_E_STATE;
+    }
+    if (t->id > w->done_id) {
+        *done = 0;
+        return LRCCS_OK;
+    }
+    const int sl = ticket_slot(w, t->id);
+    if (sl < 0) {
+        set_err(c, "lrccs_ticket_query: expired ticket (results of the last %d requests are kept)", ASYNC_SLOTS);
+        return LRCCS_E_STATE;
+    }
+    const lrccs_status st = w->slot_st[sl];
+    cudaEvent_t ev = w->slot_ev[sl];
+    lock.unlock();
+    if (st != LRCCS_OK) {
+        *done = 1;
+        return st;
+    }
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        *done = 0;
+        return LRCCS_OK;
+    }
+    *done = 1;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "lrccs_ticket_query: %s", cudaGetErrorString(e));
+        return LRCCS_E_CUDA;
+    }
+    return status_to_code(c, w->slot_dev_status[sl]);
+}
+
+extern "C" lrccs_status lrccs_ticket_wait(lrccs_ctx *c, const lrccs_ticket *t) {
+    if (!c || !t) return LRCCS_E_INVALID;
+    async_worker *w = c->worker;
+    if (!w || t->id < 1) {
+        set_err(c, "lrccs_ticket_wait: unknown ticket");
+        return LRCCS_E_STATE;
+    }
+    std::unique_lock<std::mutex> lock(w->mu);
+    if (t->id >= w->next_id) {
+        set_err(c, "lrccs_ticket_wait: unknown ticket");
+        return LRCCS_E_STATE;
+    }
+    w->cv_done.wait(lock, [&] { return w->done_id >= t->id; });
+    const int sl = ticket_slot(w, t->id);
+    if (sl < 0) {
+        set_err(c, "lrccs_ticket_wait: expired ticket (results of the last %d requests are kept)", ASYNC_SLOTS);
+        return LRCCS_E_STATE;
+    }
+    const lrccs_status st = w->slot_st[sl];
+    cudaEvent_t ev = w->slot_ev[sl];
+    lock.unlock();
+    if (st != LRCCS_OK) return st;
+    const cudaError_t e = cudaEventSynchronize(ev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "lrccs_ticket_wait: %s", cudaGetErrorString(e));
+        return LRCCS_E_CUDA;
+    }
+    return status_to_code(c, w->slot_dev_status[sl]);
 }
 
 // State buffer: this header, then U (n x r complex64).

@@ -56,6 +56,8 @@ struct prof_rec {
     bool graph_owned;   // recorded by nodes of the captured iteration graph
 };
 
+struct async_worker;   // host worker thread of the asynchronous tracking calls (api.cu)
+
 struct lrccs_ctx {
     // profiling: launches counted always; kernels in prof_mask timed with events
     long long launches[KID_COUNT];
@@ -100,6 +102,9 @@ struct lrccs_ctx {
     size_t gen_cap_q;  // frames the general-mask buffers were allocated for (0: none yet)
     int dev_smem_optin;
     int test_timeout;  // lrccs_test_wait_timeout: the next direct k_gdqr launch waits for an unreachable barrier
+    int device;        // CUDA device current at lrccs_create
+    size_t create_bytes;   // device bytes allocated by lrccs_create
+    async_worker *worker;  // started by the first lrccs_track_minibatch_async
     std::string err;
 
     // geometry / sampling

@@ -23,16 +23,22 @@ _lib = C.CDLL(LIB_PATH)
 # status codes (lrccs_status)
 OK, E_INVALID, E_NOMEM, E_CUDA, E_RANK_DEFICIENT, E_TIMEOUT, E_ADMISSION, E_STATE, E_UNSUPPORTED = range(9)
 BUF_Z, BUF_X0, BUF_GRAD, BUF_SIGMA, BUF_IDX, BUF_SCAL = range(6)
+PREC_FP32_FFT, PREC_BF16X3_GEMM, PREC_FP16S_GEMM = range(3)
 
 
 class Dims(C.Structure):
     _fields_ = [("ny", C.c_int32), ("nx", C.c_int32), ("q", C.c_int32), ("ncoil", C.c_int32),
-                ("rank", C.c_int32), ("rank_max", C.c_int32)]
+                ("rank", C.c_int32), ("rank_max", C.c_int32), ("precision", C.c_int32)]
 
 
 class Params(C.Structure):
     _fields_ = [("trunc_factor", C.c_double), ("energy_pct", C.c_double), ("eta_c", C.c_double),
-                ("eps_exit", C.c_double), ("t_max", C.c_int32), ("exit_enabled", C.c_int32)]
+                ("eps_exit", C.c_double), ("t_max", C.c_int32), ("exit_enabled", C.c_int32),
+                ("admit_reserve_bytes", C.c_double)]
+
+
+class Ticket(C.Structure):
+    _fields_ = [("id", C.c_uint64)]
 
 
 class IterInfo(C.Structure):
@@ -66,6 +72,10 @@ _sig = {
     "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
+    "lrccs_context_bytes": (_st, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "lrccs_track_minibatch_async": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.c_void_p]),
+    "lrccs_ticket_query": (_st, [_vp, C.c_void_p, C.POINTER(C.c_int32)]),
+    "lrccs_ticket_wait": (_st, [_vp, C.c_void_p]),
     "lrccs_mec1": (_st, [_vp, C.c_int32, _vp, _vp, _vp]),
     "lrccs_mec2": (_st, [_vp, C.c_int32, C.c_double, C.c_double, _vp, _vp, _vp, C.POINTER(C.c_int32)]),
     "lrccs_online_frames": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp]),
@@ -106,9 +116,16 @@ def default_params() -> Params:
     return p
 
 
-def lrccs_create(ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None):
+def lrccs_context_bytes(ny, nx, q, ncoil, rank, rank_max=0, precision=PREC_FP32_FFT) -> int:
+    d = Dims(ny, nx, q, ncoil, rank, rank_max, precision)
+    b = C.c_size_t(0)
+    _check(None, _lib.lrccs_context_bytes(C.byref(d), C.byref(b)))
+    return b.value
+
+
+def lrccs_create(ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None, precision=PREC_FP32_FFT):
     """Returns an opaque context handle (int).  `stream` is a torch.cuda.Stream or None."""
-    d = Dims(ny, nx, q, ncoil, rank, rank_max)
+    d = Dims(ny, nx, q, ncoil, rank, rank_max, precision)
     p = params if params is not None else default_params()
     h = _vp()
     s = None if stream is None else _vp(stream.cuda_stream)
@@ -217,6 +234,24 @@ def lrccs_track_minibatch(ctx, y, frame_ptr, mask, smaps, t_max: int, reset_eta:
     _check(ctx, _lib.lrccs_track_minibatch(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps), int(t_max),
                                            1 if reset_eta else 0, _ptr(X), C.byref(inf) if info else None))
     return _info_dict(inf) if info else None
+
+
+def lrccs_track_minibatch_async(ctx, y, frame_ptr, mask, smaps, t_max: int, reset_eta: bool = False, X=None):
+    """Enqueue one tracking request on the context's worker; returns its Ticket."""
+    t = Ticket()
+    _check(ctx, _lib.lrccs_track_minibatch_async(ctx, _ptr(y), _ptr(frame_ptr), _ptr(mask), _ptr(smaps),
+                                                 int(t_max), 1 if reset_eta else 0, _ptr(X), C.byref(t)))
+    return t
+
+
+def lrccs_ticket_query(ctx, ticket) -> bool:
+    done = C.c_int32(0)
+    _check(ctx, _lib.lrccs_ticket_query(ctx, C.byref(ticket), C.byref(done)))
+    return bool(done.value)
+
+
+def lrccs_ticket_wait(ctx, ticket):
+    _check(ctx, _lib.lrccs_ticket_wait(ctx, C.byref(ticket)))
 
 
 def lrccs_get_state(ctx) -> bytes:

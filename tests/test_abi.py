@@ -121,3 +121,37 @@ def test_noalloc_wrapper_validates_before_any_launch(lib):
     for yy, cnt, gg in bad:
         with pytest.raises(ValueError):
             lrccs.lrccs_trunc_threshold_noalloc(yy, cnt, 36.0, gg)
+
+
+def test_context_bytes_without_a_gpu(lib):
+    """lrccs_context_bytes sizes a context from its dims alone (no allocation):
+    it grows with q, C and the rank, and covers at least Z, X0 and the
+    transform work buffer (complex64)."""
+    from paper_2212_09664_gb300 import lrccs
+
+    b = lrccs.lrccs_context_bytes(192, 192, 48, 12, 10)
+    n = 192 * 192
+    assert b >= 8 * (2 * n * 48 + 12 * n * 10)
+    assert lrccs.lrccs_context_bytes(192, 192, 96, 12, 10) > b
+    assert lrccs.lrccs_context_bytes(192, 192, 48, 20, 10) > b
+    assert lrccs.lrccs_context_bytes(192, 192, 48, 12, 14) > b
+
+
+@pytest.mark.parametrize("prec", [1, 2, 7])
+def test_unbuilt_precision_forms_are_refused(lib, prec):
+    from paper_2212_09664_gb300 import lrccs
+
+    with pytest.raises(lrccs.LrccsError) as ei:
+        lrccs.lrccs_create(64, 64, 8, 2, 2, precision=prec)
+    assert ei.value.status == lrccs.E_UNSUPPORTED
+
+
+def test_ticket_calls_reject_unknown_tickets_without_a_context(lib):
+    from paper_2212_09664_gb300 import lrccs
+
+    L = lrccs._lib
+    t = lrccs.Ticket(1)
+    d = C.c_int32(0)
+    assert L.lrccs_ticket_query(None, C.byref(t), C.byref(d)) == lrccs.E_INVALID
+    assert L.lrccs_ticket_wait(None, C.byref(t)) == lrccs.E_INVALID
+    assert L.lrccs_track_minibatch_async(None, None, None, None, None, 5, 0, None, C.byref(t)) == lrccs.E_INVALID
