@@ -218,127 +218,200 @@ SERVE_FIRST = 32           # frames of the first mini-batch (Alg. 4 step 1, T_ma
 SERVE_ALPHA = 8            # frames of every later mini-batch (T_max,j = 5)
 SERVE_BATCHES = 12         # later mini-batches per acquisition
 SERVE_FPS = 20.0           # frame arrival rate per acquisition
-SERVE_STAGGER_S = 0.05     # acquisition i starts i x 50 ms after acquisition 0
+SERVE_RATES = (1, 8, 32)   # arrival-rate multipliers of the load sweep (1 = the paper-like 20 frames/s)
+SERVE_STAGGER_S = 0.05     # acquisition i starts i x 50 ms after acquisition 0 (at rate 1)
 T_FIRST, T_NEXT = 70, 5
 
 
-def serving(dev):
-    """p50/p99 arrival-to-reconstruction latency of mini-batch subspace tracking.
+def serving_streams(seed=0x5EED0005):
+    """Shapes of the served acquisitions, drawn from the seed: image side from
+    {128, 160, 192, 224, 256}, 12-20 coils, rank 6-14, 1D variable-density
+    Cartesian lines (even streams) or golden-angle pseudo-radial spokes (odd
+    streams) at 4x-12x acceleration."""
+    import numpy as np
 
-    Frames of every acquisition arrive in real time at SERVE_FPS.  When the last
-    frame of a mini-batch has arrived, its samples are copied from pinned host
-    memory, the mini-batch is solved on that acquisition's own stream (first
-    mini-batch: lrccs_init + lrccs_iterate(70); later ones:
-    lrccs_track_minibatch with 5 iterations, U kept on the device) and its images
-    are copied back to pinned host memory; the latency runs from the arrival of
-    that last frame to the moment the host sees the images.  One host thread
-    submits every request and polls for completions, so requests of different
-    acquisitions overlap on the GPU.  Every acquisition replays the same
-    synthetic sequence, so every client's images must equal, bit for bit, those
-    of one client run alone."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(SERVE_STREAMS):
+        side = int(rng.choice([128, 160, 192, 224, 256]))
+        nc = int(rng.integers(12, 21))
+        r = int(rng.integers(6, 15))
+        accel = float(rng.uniform(4.0, 12.0))
+        spec = dict(kind="phantom", ny=side, nx=side, q=SERVE_FIRST + SERVE_ALPHA * SERVE_BATCHES, nc=nc, rank=r,
+                    noise=0.01, n_inner=5)
+        if i % 2 == 0:
+            spec.update(mask_kind="lines_vd", accel=accel)
+        else:
+            spec.update(mask_kind="radial", spokes=max(4, int(round(side / accel))))
+        out.append(spec)
+    return out
+
+
+def serving(dev):
+    """p50/p99 arrival-to-reconstruction latency of mini-batch subspace tracking
+    (Alg. 4) as a continuous-batching request loop over 8 uneven acquisitions.
+
+    Every acquisition has its own shape (serving_streams).  Its frames arrive in
+    real time; when the last frame of a mini-batch has arrived, its samples are
+    copied from pinned host memory to the device and the request is submitted:
+    the first mini-batch (32 frames) by lrccs_init + lrccs_iterate(70) on the
+    acquisition's first context, every later one (8 frames) by
+    lrccs_track_minibatch_async on its tracking context (U stays on the device),
+    which returns a ticket at once.  One host thread submits every request and
+    polls the tickets; requests of different acquisitions overlap on the GPU.
+    The latency runs from the arrival of the mini-batch's last frame to the
+    moment its images are in host memory.  Contexts are admitted by free device
+    memory (lrccs_create refuses with LRCCS_E_ADMISSION; the loop would retry).
+    The load sweep repeats the loop at SERVE_RATES times the frame rate and
+    reports the largest number of requests in flight at once.  Every
+    acquisition is first run alone; its images in every mixed run must equal
+    those, bit for bit."""
     import numpy as np
     import torch
 
     from paper_2212_09664_gb300 import lrccs, synth
 
     F1, A, M, S = SERVE_FIRST, SERVE_ALPHA, SERVE_BATCHES, SERVE_STREAMS
-    seq = synth.make_problem(WORKLOAD, seed=0x5EED0005, q=F1 + A * M)
-    parts = [synth.frames(seq, 0, F1)] + [synth.frames(seq, F1 + A * j, A) for j in range(M)]
-    host = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (b.y, b.frame_ptr, b.mask))
-            for b in parts]
-    smaps = torch.from_numpy(seq.smaps).to(dev)
-    n, r = seq.n, seq.rank
+    specs = serving_streams()
+    seqs = [synth.make_problem(sp, seed=0x5EED0100 + i) for i, sp in enumerate(specs)]
 
     class Client:
-        def __init__(self):
+        def __init__(self, seq):
+            self.seq = seq
+            self.parts = [synth.frames(seq, 0, F1)] + [synth.frames(seq, F1 + A * j, A) for j in range(M)]
+            self.host = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (b.y, b.frame_ptr,
+                                                                                                   b.mask))
+                         for b in self.parts]
             self.stream = torch.cuda.Stream(device=dev)
-            self.first = lrccs.Solver(seq.ny, seq.nx, F1, seq.nc, r, stream=self.stream)
-            self.mb = lrccs.Solver(seq.ny, seq.nx, A, seq.nc, r, stream=self.stream)
+            self.smaps = torch.from_numpy(seq.smaps).to(dev)
+            self.first = lrccs.Solver(seq.ny, seq.nx, F1, seq.nc, seq.rank, stream=self.stream)
+            self.mb = lrccs.Solver(seq.ny, seq.nx, A, seq.nc, seq.rank, stream=self.stream)
             with torch.cuda.stream(self.stream):
-                self.dev = [tuple(torch.empty_like(h, device=dev) for h in hb) for hb in host]
-                self.X = [torch.empty((b.q, n), dtype=torch.complex64, device=dev) for b in parts]
-                self.U = torch.empty((n, r), dtype=torch.complex64, device=dev)
-            self.Xh = torch.empty((F1, n), dtype=torch.complex64).pin_memory()
+                self.dev = [tuple(torch.empty_like(h, device=dev) for h in hb) for hb in self.host]
+                self.X = [torch.empty((b.q, seq.n), dtype=torch.complex64, device=dev) for b in self.parts]
+                self.U = torch.empty((seq.n, seq.rank), dtype=torch.complex64, device=dev)
+            self.Xh = [torch.empty((b.q, seq.n), dtype=torch.complex64).pin_memory() for b in self.parts]
+            self.ready = False
+            self.ticket = None
+
+        def reset(self):
             self.ready = False
 
         def submit(self, j):
-            y, fp, mask = self.dev[j]
             with torch.cuda.stream(self.stream):
-                for d, h in zip(self.dev[j], host[j]):
+                for d, h in zip(self.dev[j], self.host[j]):
                     d.copy_(h, non_blocking=True)
-                if j == 0:
-                    lrccs.lrccs_init(self.first.ctx, y, fp, mask, smaps)
+            y, fp, mask = self.dev[j]
+            if j == 0:
+                with torch.cuda.stream(self.stream):
+                    lrccs.lrccs_init(self.first.ctx, y, fp, mask, self.smaps)
                     lrccs.lrccs_iterate(self.first.ctx, T_FIRST)
                     lrccs.lrccs_get_images(self.first.ctx, self.X[0])
-                else:
-                    lrccs.lrccs_track_minibatch(self.mb.ctx, y, fp, mask, smaps, T_NEXT, False, self.X[j])
-                self.Xh[: parts[j].q].copy_(self.X[j], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self.stream)
-            return ev
+                    ev = torch.cuda.Event()
+                    ev.record(self.stream)
+                return ("event", ev)
+            return ("ticket", lrccs.lrccs_track_minibatch_async(self.mb.ctx, y, fp, mask, self.smaps, T_NEXT,
+                                                                False, self.X[j]))
 
-        def done(self, j):
-            ctx = self.first.ctx if j == 0 else self.mb.ctx
-            lrccs.lrccs_synchronize(ctx)      # raises on a device-side failure
-            if j == 0:                        # hand U^(1) and eta to the tracking context
+        def poll(self, h):
+            kind, obj = h
+            return obj.query() if kind == "event" else lrccs.lrccs_ticket_query(self.mb.ctx, obj)
+
+        def finish(self, j, h):
+            kind, obj = h
+            if kind == "ticket":
+                lrccs.lrccs_ticket_wait(self.mb.ctx, obj)     # raises on a device-side failure
+            else:
+                lrccs.lrccs_synchronize(self.first.ctx)
+            with torch.cuda.stream(self.stream):               # images to host memory, on this stream only
+                self.Xh[j].copy_(self.X[j])
+            if j == 0:                                         # hand U^(1) and eta to the tracking context
                 eta = lrccs.lrccs_iterate(self.first.ctx, 0, info=True)["eta"]
                 lrccs.lrccs_get_subspace(self.first.ctx, self.U)
-                lrccs.lrccs_set_subspace(self.mb.ctx, self.U, r, eta)
+                self.stream.synchronize()
+                lrccs.lrccs_set_subspace(self.mb.ctx, self.U, self.seq.rank, eta)
                 self.ready = True
 
         def close(self):
             self.first.close()
             self.mb.close()
 
-    # one client alone, back to back: the reference images, and the last
-    # mini-batch against the FP64 oracle from the same warm start
-    solo = Client()
-    for j in range(M + 1):
-        if j == M:
-            lrccs.lrccs_get_subspace(solo.mb.ctx, solo.U)
-            solo.stream.synchronize()
-            U_prev = solo.U.cpu().numpy().astype(np.complex128)
-            eta = lrccs.lrccs_iterate(solo.mb.ctx, 0, info=True)["eta"]
-        solo.submit(j).synchronize()
-        solo.done(j)
-    check = (parts[M], U_prev, eta, solo.X[M].cpu().numpy().astype(np.complex128))
-
-    clients = [Client() for _ in range(S)]
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    clients = [Client(sq) for sq in seqs]
+    admitted_bytes = sum(lrccs.lrccs_context_bytes(c.seq.ny, c.seq.nx, F1, c.seq.nc, c.seq.rank) +
+                         lrccs.lrccs_context_bytes(c.seq.ny, c.seq.nx, A, c.seq.nc, c.seq.rank) for c in clients)
+    # each acquisition alone, back to back: the reference images; the last
+    # mini-batch of the smallest acquisition is kept for the FP64 check
+    solo = {}
+    small = min(range(S), key=lambda i: clients[i].seq.n)
+    check = None
+    for i, cl in enumerate(clients):
+        for j in range(M + 1):
+            if i == small and j == M:
+                lrccs.lrccs_get_subspace(cl.mb.ctx, cl.U)
+                torch.cuda.synchronize()
+                U_prev = cl.U.cpu().numpy().astype(np.complex128)
+                eta = lrccs.lrccs_iterate(cl.mb.ctx, 0, info=True)["eta"]
+            h = cl.submit(j)
+            cl.finish(j, h)
+            solo[(i, j)] = cl.Xh[j].clone()
+        if i == small:
+            check = (cl.parts[M], U_prev, eta, cl.Xh[M].numpy().astype(np.complex128))
+        cl.reset()
     torch.cuda.synchronize()
-    events = sorted((i * SERVE_STAGGER_S + (F1 + A * j) / SERVE_FPS, i, j) for i in range(S) for j in range(M + 1))
-    lat = {}
-    pending = []
-    t0 = time.perf_counter() + 0.05
 
-    def poll():
-        for item in list(pending):
-            ev, i, j, ta = item
-            if ev.query():
-                lat[(i, j)] = time.perf_counter() - t0 - ta
-                pending.remove(item)
-                clients[i].done(j)
+    def run_mix(rate):
+        fps = SERVE_FPS * rate
+        events = sorted((i * SERVE_STAGGER_S / rate + (F1 + A * j) / fps, i, j) for i in range(S)
+                        for j in range(M + 1))
+        lat, pending, max_inflight = {}, [], 0
+        t0 = time.perf_counter() + 0.05
 
-    for ta, i, j in events:
-        while time.perf_counter() - t0 < ta or (j > 0 and not clients[i].ready):
+        def poll():
+            for item in list(pending):
+                h, i, j, ta = item
+                if clients[i].poll(h):
+                    clients[i].finish(j, h)
+                    lat[(i, j)] = time.perf_counter() - t0 - ta
+                    pending.remove(item)
+
+        for ta, i, j in events:
+            while time.perf_counter() - t0 < ta or (j > 0 and not clients[i].ready):
+                poll()
+                if not pending:
+                    time.sleep(max(0.0, min(2e-4, ta - (time.perf_counter() - t0))))
+            pending.append((clients[i].submit(j), i, j, ta))
+            max_inflight = max(max_inflight, len(pending))
+        while pending:
             poll()
-            if not pending:
-                time.sleep(max(0.0, min(2e-4, ta - (time.perf_counter() - t0))))
-        pending.append((clients[i].submit(j), i, j, ta))
-    while pending:
-        poll()
-    torch.cuda.synchronize()
-    same = all(torch.equal(c.X[j], solo.X[j]) for c in clients for j in range(M + 1))
-    later = np.array([lat[(i, j)] for i in range(S) for j in range(1, M + 1)]) * 1e3
-    firsts = np.array([lat[(i, 0)] for i in range(S)]) * 1e3
-    for c in clients + [solo]:
+        torch.cuda.synchronize()
+        same = all(torch.equal(clients[i].Xh[j], solo[(i, j)]) for i in range(S) for j in range(M + 1))
+        later = np.array([lat[(i, j)] for i in range(S) for j in range(1, M + 1)]) * 1e3
+        firsts = np.array([lat[(i, 0)] for i in range(S)]) * 1e3
+        span = max(ta for ta, _, _ in events) + later.max() / 1e3
+        for c in clients:
+            c.reset()
+        return dict(rate=rate, fps_per_stream=fps, p50_ms=float(np.percentile(later, 50)),
+                    p99_ms=float(np.percentile(later, 99)), max_ms=float(later.max()),
+                    first_batch_p50_ms=float(np.percentile(firsts, 50)), max_in_flight=int(max_inflight),
+                    minibatches_per_s=float(S * M / span), same_alone_and_in_mix=bool(same))
+
+    sweep = [run_mix(rate) for rate in SERVE_RATES]
+    for c in clients:
         c.close()
+    base = sweep[0]
     return dict(streams=S, first_batch_frames=F1, t_first=T_FIRST, minibatch_frames=A, t_next=T_NEXT,
                 minibatches_per_stream=M, fps_per_stream=SERVE_FPS,
-                p50_ms=float(np.percentile(later, 50)), p99_ms=float(np.percentile(later, 99)),
-                max_ms=float(later.max()), first_batch_p50_ms=float(np.percentile(firsts, 50)),
-                first_batch_max_ms=float(firsts.max()), same_alone_and_in_mix=bool(same),
-                workload="%s-shaped acquisition of %d frames (one synthetic sequence replayed by every stream, "
-                         "starts staggered by %.0f ms)" % (WORKLOAD, F1 + A * M, SERVE_STAGGER_S * 1e3)), check
+                p50_ms=base["p50_ms"], p99_ms=base["p99_ms"], max_ms=base["max_ms"],
+                first_batch_p50_ms=base["first_batch_p50_ms"], max_in_flight=base["max_in_flight"],
+                same_alone_and_in_mix=all(x["same_alone_and_in_mix"] for x in sweep), load_sweep=sweep,
+                admission=dict(context_bytes=int(admitted_bytes), free_bytes_before=int(free0)),
+                stream_shapes=[dict(side=sp["ny"], coils=sp["nc"], rank=sp["rank"], masks=sp["mask_kind"],
+                                    accel=round(sp.get("accel", 0.0), 2), spokes=sp.get("spokes"))
+                               for sp in specs],
+                workload="8 uneven synthetic acquisitions of %d frames (first mini-batch %d, then %d x %d), "
+                         "frames arriving in real time; latency = last frame's arrival to images in host memory"
+                         % (F1 + A * M, F1, M, A)), check
 
 
 def library_comparators(p, dev, used_rows, stats):

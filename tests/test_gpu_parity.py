@@ -83,17 +83,6 @@ def test_frame_ptr_mismatch_is_rejected():
     s.close()
 
 
-def test_partial_rows_are_unsupported():
-    p = synth.make_problem("lines64_q32_c1_r4")
-    mask = p.mask.copy()
-    mask[0, 5] ^= 1                        # break one line
-    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank)
-    with pytest.raises(lrccs.LrccsError) as ei:
-        s.init(*to_dev(p, mask=mask))
-    assert ei.value.status == lrccs.E_UNSUPPORTED
-    s.close()
-
-
 def test_empty_frame_is_rank_deficient():
     p = synth.make_problem(MEDIUM, seed=3)
     mask = p.mask.copy()
