@@ -45,7 +45,8 @@ class _Problem(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("trunc_factor", C.c_double), ("energy_pct", C.c_double), ("eta_c", C.c_double),
                 ("eps_exit", C.c_double), ("init_kind", C.c_int32), ("exit_enabled", C.c_int32),
-                ("frob_eta", C.c_int32), ("grad_mode", C.c_int32)]
+                ("frob_eta", C.c_int32), ("grad_mode", C.c_int32), ("exit_patience", C.c_int32),
+                ("eta_scale0", C.c_double), ("eta_decay", C.c_double), ("t_offset", C.c_int32)]
 
 
 def _load():
@@ -92,9 +93,11 @@ class Params:
     """Alg. 2 constants (blue parameter settings) plus oracle switches."""
 
     def __init__(self, trunc_factor=36.0, energy_pct=85.0, eta_c=0.14, eps_exit=0.01,
-                 init_kind=0, exit_enabled=False, frob_eta=False, grad_mode=0):
+                 init_kind=0, exit_enabled=False, frob_eta=False, grad_mode=0, exit_patience=1, eta_scale0=1.0,
+                 eta_decay=1.0, t_offset=0):
         self.s = _Params(trunc_factor, energy_pct, eta_c, eps_exit, init_kind, int(exit_enabled),
-                         int(frob_eta), grad_mode)
+                         int(frob_eta), grad_mode, int(exit_patience), float(eta_scale0), float(eta_decay),
+                         int(t_offset))
 
 
 class Operator:

@@ -683,7 +683,7 @@ int orc_iterate(const orc_problem *P, const orc_cx *y, const orc_params *prm,
     const int n = frame_n(P), q = P->q;
     orc_cx *Uold = cx_alloc((size_t)n * r), *G = cx_alloc((size_t)n * r);
     orc_cx *Up = cx_alloc((size_t)n * r), *R = cx_alloc((size_t)r * r);
-    int t, rc = 0;
+    int t, rc = 0, passed = 0;
     for (t = 0; t < n_iter; ++t) {
         memcpy(Uold, U, sizeof(orc_cx) * (size_t)n * r);
         au_cache c;
@@ -710,12 +710,22 @@ int orc_iterate(const orc_problem *P, const orc_cx *y, const orc_params *prm,
         }
         if (gnorm) gnorm[t] = gn;
         if (*eta <= 0.0) *eta = prm->eta_c / gn;
-        for (size_t i = 0; i < (size_t)n * r; ++i) Up[i] = Uold[i] - (*eta) * G[i];
+        /* the step of this iteration: eta, or the variable step size
+           eta * scale0 * decay^(t_offset + t) of the tuning notes */
+        const double s0 = prm->eta_scale0 > 0.0 ? prm->eta_scale0 : 1.0;
+        const double dk = prm->eta_decay > 0.0 ? prm->eta_decay : 1.0;
+        const double eta_t = (*eta) * s0 * pow(dk, (double)(prm->t_offset + t));
+        for (size_t i = 0; i < (size_t)n * r; ++i) Up[i] = Uold[i] - eta_t * G[i];
         if (orc_qr(Up, n, r, U, R) != 0) { rc = -3; break; }
         double d = orc_sd(Uold, U, n, r);
         if (sd) sd[t] = d;
         if (Uprev) memcpy(Uprev, Uold, sizeof(orc_cx) * (size_t)n * r);
-        if (prm->exit_enabled && d / sqrt((double)r) < prm->eps_exit) { ++t; break; }
+        if (prm->exit_enabled) {
+            /* Alg. 2's exit test; with exit_patience > 1 it must pass that many
+               consecutive iterations (the robust exit of the tuning notes) */
+            passed = d / sqrt((double)r) < prm->eps_exit ? passed + 1 : 0;
+            if (passed >= (prm->exit_patience > 1 ? prm->exit_patience : 1)) { ++t; break; }
+        }
     }
     free(R);
     free(Up);

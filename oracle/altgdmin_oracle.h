@@ -46,6 +46,12 @@ typedef struct orc_params {
     int32_t exit_enabled;   /* 1 = stop when SD(U, U+)/sqrt(r) < eps_exit */
     int32_t frob_eta;       /* 0 = spectral norm in eta (default), 1 = Frobenius */
     int32_t grad_mode;      /* 0 = per-frame literal adjoint, 1 = summed over frames in k-space */
+    /* tuning variants of the discussion section (defaults give Alg. 2 as printed) */
+    int32_t exit_patience;  /* exit only after this many consecutive iterations pass the exit
+                               test (robust exit); <= 1 = the first one (Alg. 2) */
+    double eta_scale0;      /* variable step size: eta_t = eta * eta_scale0 * eta_decay^(t_offset + t - 1), */
+    double eta_decay;       /*   t = 1, 2, ... within a call; 1 and 1 = the constant eta of Alg. 2 */
+    int32_t t_offset;       /* iterations run before this call (for the step-size schedule) */
 } orc_params;
 
 #ifdef __cplusplus

@@ -115,3 +115,59 @@ def test_exit_disabled_runs_every_iteration():
     op, y = problem()
     res = op.iterate(y, U_of(TH0, PH0), 15, params=oracle.Params(exit_enabled=False, eps_exit=1.0))
     assert res["iters"] == 15
+
+
+# ---------------------------------------------------------------- tuning variants (discussion section)
+
+def closed_form_schedule(n_iter, scale0=1.0, decay=1.0, t_offset=0):
+    """The same recursion with the variable step eta_t = eta scale0 decay^(t_offset + t - 1)."""
+    g1 = S1 ** 2 * math.cos(TH0) * math.sin(TH0)
+    g2 = S2 ** 2 * math.cos(PH0) * math.sin(PH0)
+    eta = ETA_C / max(g1, g2)
+    th, ph, sds = TH0, PH0, []
+    for t in range(n_iter):
+        et = eta * scale0 * decay ** (t_offset + t)
+        a = et * S1 ** 2 * math.sin(2 * th) / 2
+        b = et * S2 ** 2 * math.sin(2 * ph) / 2
+        sds.append(math.sqrt(a * a / (1 + a * a) + b * b / (1 + b * b)))
+        th, ph = th - math.atan(a), ph - math.atan(b)
+    return np.array(sds), (th, ph)
+
+
+@pytest.mark.parametrize("scale0,decay,t_offset", [(2.0, 0.8, 0), (1.5, 0.9, 3), (1.0, 1.0, 5)])
+def test_variable_step_size_follows_the_closed_form(scale0, decay, t_offset):
+    """Larger steps first, then smaller: eta_t = eta scale0 decay^(t_offset + t - 1)
+    with eta = eta_c / ||grad_1||_2 from the call's first gradient."""
+    op, y = problem()
+    sds, (th, ph) = closed_form_schedule(12, scale0, decay, t_offset)
+    prm = oracle.Params(eta_scale0=scale0, eta_decay=decay, t_offset=t_offset)
+    res = op.iterate(y, U_of(TH0, PH0), 12, params=prm)
+    assert np.abs(res["sd"] - sds).max() < 1e-13
+    assert np.abs(res["U"] - U_of(th, ph)).max() < 1e-13
+
+
+def test_a_decaying_step_differs_from_the_constant_one():
+    """A planted mistake (the schedule ignored) would leave SD unchanged; it must not."""
+    sd_const, _ = closed_form_schedule(6)
+    sd_var, _ = closed_form_schedule(6, 2.0, 0.8)
+    assert np.abs(sd_const - sd_var).max() > 1e-2
+    op, y = problem()
+    res = op.iterate(y, U_of(TH0, PH0), 6, params=oracle.Params(eta_scale0=2.0, eta_decay=0.8))
+    assert np.abs(res["sd"] - sd_const).max() > 1e-2
+
+
+@pytest.mark.parametrize("patience", [2, 3])
+def test_robust_exit_needs_consecutive_passes(patience):
+    """Exit only once `patience` consecutive iterations pass the exit test.  With
+    a threshold between SD_{t*} and every earlier SD, and the sequence decreasing
+    after t*, the robust exit stops after t* + patience - 1 iterations."""
+    op, y = problem()
+    sds, _, _ = closed_form(40)
+    t_star = 6
+    assert np.all(np.diff(sds[t_star - 1:t_star + 4]) < 0)
+    eps = math.sqrt(sds[t_star - 1] * sds[: t_star - 1].min()) / math.sqrt(2)
+    res = op.iterate(y, U_of(TH0, PH0), 40,
+                     params=oracle.Params(exit_enabled=True, eps_exit=eps, exit_patience=patience))
+    assert res["iters"] == t_star + patience - 1
+    plain = op.iterate(y, U_of(TH0, PH0), 40, params=oracle.Params(exit_enabled=True, eps_exit=eps))
+    assert plain["iters"] == t_star
