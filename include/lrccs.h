@@ -90,6 +90,13 @@ typedef struct lrccs_params {
     int32_t exit_enabled;  /* 1: lrccs_iterate stops at the exit test (one host sync per iteration) */
     double admit_reserve_bytes;  /* 256 MiB: device memory that must stay free after lrccs_create's
                                     buffers, or the context is not admitted (LRCCS_E_ADMISSION) */
+    /* tuning variants from the paper's discussion of its limitations (the
+       defaults give Alg. 2 as printed) */
+    int32_t exit_patience; /* 1    : with exit_enabled, stop once this many consecutive iterations
+                                     pass the exit test (a more robust exit) */
+    int32_t reserved;
+    double eta_scale0;     /* 1    : variable step size eta_t = eta * eta_scale0 * eta_decay^k, */
+    double eta_decay;      /* 1    :   k = iterations since eta was set (larger steps first) */
 } lrccs_params;
 
 typedef struct lrccs_iter_info {
@@ -100,8 +107,8 @@ typedef struct lrccs_iter_info {
     double gnorm;       /* ||grad||_2 of the first iteration (defines eta) */
 } lrccs_iter_info;
 
-/* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off) and a
- * 256 MiB admission reserve. */
+/* Fill p with the paper's constants (36, 85, 0.14, 0.01, 70, exit off), a
+ * 256 MiB admission reserve, exit_patience 1 and a constant step size. */
 void lrccs_default_params(lrccs_params *p);
 
 /* Create a context for one problem size on the current CUDA device.  The rank

@@ -52,6 +52,10 @@ extern "C" void lrccs_default_params(lrccs_params *p) {
     p->t_max = 70;
     p->exit_enabled = 0;
     p->admit_reserve_bytes = 268435456.0;
+    p->exit_patience = 1;
+    p->reserved = 0;
+    p->eta_scale0 = 1.0;
+    p->eta_decay = 1.0;
 }
 
 extern "C" const char *lrccs_status_string(lrccs_status s) {
@@ -537,7 +541,8 @@ static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
 // graph when none matches (lrccs_iterate); otherwise replay one only when it
 // already matches (tracking calls, whose sampled rows change every call).
 static lrccs_status run_iterations(lrccs_ctx *c, int n_iter, bool may_capture, lrccs_iter_info *info) {
-    int exited = 0;
+    int exited = 0, passed = 0;
+    const int patience = c->prm.exit_patience > 1 ? c->prm.exit_patience : 1;
     // without the per-iteration exit test, replay the captured n-iteration graph
     // (the same kernels, launched with fewer gaps); timing events, when
     // requested, are nodes of the graph and report its latest replay
@@ -556,7 +561,8 @@ static lrccs_status run_iterations(lrccs_ctx *c, int n_iter, bool may_capture, l
             double sd = 0.0;
             CK(cudaMemcpyAsync(&sd, c->d_scal + SC_SD, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
-            if (sd / sqrt((double)c->r) < c->prm.eps_exit) {
+            passed = sd / sqrt((double)c->r) < c->prm.eps_exit ? passed + 1 : 0;
+            if (passed >= patience) {
                 exited = 1;
                 break;
             }
@@ -608,6 +614,7 @@ extern "C" lrccs_status lrccs_set_subspace(lrccs_ctx *c, const void *d_U, int32_
     CK(cudaMemcpyAsync(c->d_scal + SC_ETA, &eta_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_scal + SC_ETASET, &set_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_scal + SC_GNORM, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_TCNT, &zero, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->r = rank;
     c->t = 0;
@@ -630,7 +637,10 @@ extern "C" lrccs_status lrccs_track_minibatch(lrccs_ctx *c, const void *d_y, con
     }
     c->initialized = 0;
     // Alg. 4: the initialisation of Alg. 2 is replaced by U_0 <- U^(j-1)
-    if (reset_eta) CK(cudaMemsetAsync(c->d_scal + SC_ETASET, 0, sizeof(double), c->stream));
+    if (reset_eta) {
+        CK(cudaMemsetAsync(c->d_scal + SC_ETASET, 0, sizeof(double), c->stream));
+        CK(cudaMemsetAsync(c->d_scal + SC_TCNT, 0, sizeof(double), c->stream));
+    }
     lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, false);
     if (s != LRCCS_OK) return s;
     s = warm_start(c);
@@ -1072,7 +1082,7 @@ extern "C" lrccs_status lrccs_ticket_wait(lrccs_ctx *c, const lrccs_ticket *t) {
 // State buffer: this header, then U (n x r complex64).
 struct state_header {
     uint32_t magic, version;
-    int32_t ny, nx, r, t, eta_set, reserved;
+    int32_t ny, nx, r, t, eta_set, tcnt;   // tcnt: iterations since eta was set (step-size schedule)
     double eta, gnorm;
     uint8_t pad[16];
 };
@@ -1112,6 +1122,7 @@ extern "C" lrccs_status lrccs_get_state(lrccs_ctx *c, void *host_buf, size_t *by
     h.r = c->r;
     h.t = c->t;
     h.eta_set = sc[SC_ETASET] != 0.0 ? 1 : 0;
+    h.tcnt = (int32_t)sc[SC_TCNT];
     h.eta = sc[SC_ETA];
     h.gnorm = sc[SC_GNORM];
     memcpy(host_buf, &h, sizeof(h));
@@ -1141,12 +1152,13 @@ extern "C" lrccs_status lrccs_set_state(lrccs_ctx *c, const void *host_buf, size
         set_err(c, "lrccs_set_state: buffer holds %zu bytes, %zu needed", bytes, sizeof(state_header) + ub);
         return LRCCS_E_INVALID;
     }
-    const double set_v = h.eta_set ? 1.0 : 0.0;
+    const double set_v = h.eta_set ? 1.0 : 0.0, tcnt_v = h.tcnt > 0 ? (double)h.tcnt : 0.0;
     CK(cudaMemcpyAsync(c->d_U, (const char *)host_buf + sizeof(state_header), ub, cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaMemcpyAsync(c->d_scal + SC_ETA, &h.eta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_scal + SC_GNORM, &h.gnorm, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_scal + SC_ETASET, &set_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_scal + SC_TCNT, &tcnt_v, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->r = h.r;
     c->t = h.t;

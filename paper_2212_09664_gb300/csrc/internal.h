@@ -17,6 +17,7 @@ enum {
     SC_GNORM = 3,   // ||grad||_2 of the iteration that set eta
     SC_MBAR = 4,    // mean samples per coil
     SC_ETASET = 5,  // 1 once eta is set
+    SC_TCNT = 6,    // iterations run since eta was set (variable step-size schedule)
     SC_COUNT = 8
 };
 

@@ -49,6 +49,7 @@ struct GdArgs {
     unsigned int *status;
     int n, r, q, zs, chunk, resident, mode;
     double eta_c;
+    double eta_scale0, eta_decay;   // variable step size: eta_t = eta eta_scale0 eta_decay^k
     unsigned int spin_limit;   // polls before a grid barrier gives up (2^24 normally)
     unsigned int bar_skew;     // extra arrivals a barrier waits for (0; 1 only for the timeout test)
 };
@@ -313,6 +314,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     // every block has passed the first barrier (so after every block read it)
     const double eta_in = a.scal[SC_ETA];
     const bool eta_set = a.scal[SC_ETASET] != 0.0;
+    const double tcnt = eta_set ? a.scal[SC_TCNT] : 0.0;   // iterations since eta was set
 
     // ------------------------------------------------ phase 1: gradient and Gram partial sums
     // tiles: [grad^H grad (upper tiles) | U^H grad (all) | U^H U (upper tiles)], init: [U+^H U+]
@@ -469,6 +471,13 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
                     a.scal[SC_ETASET] = 1.0;
                 }
             }
+        }
+        // the step of this iteration (constant unless a schedule is set), and
+        // the schedule's counter for the next one (every block has read it)
+        if (t == 0) {
+            if (a.eta_scale0 != 1.0 || a.eta_decay != 1.0)
+                s_eta = (float)((double)s_eta * a.eta_scale0 * pow(a.eta_decay, tcnt));
+            if (blockIdx.x == 0) a.scal[SC_TCNT] = tcnt + 1.0;
         }
         __syncthreads();
         const float eta = s_eta, eta2 = s_eta * s_eta;
@@ -684,6 +693,8 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.resident = chunk >= per ? 1 : 0;
     a.mode = mode;
     a.eta_c = c->prm.eta_c;
+    a.eta_scale0 = c->prm.eta_scale0 > 0.0 ? c->prm.eta_scale0 : 1.0;
+    a.eta_decay = c->prm.eta_decay > 0.0 ? c->prm.eta_decay : 1.0;
     a.spin_limit = 1u << 24;
     a.bar_skew = 0;
     if (c->test_timeout && !c->capturing) {   // lrccs_test_wait_timeout: this launch only

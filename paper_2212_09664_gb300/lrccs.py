@@ -34,7 +34,8 @@ class Dims(C.Structure):
 class Params(C.Structure):
     _fields_ = [("trunc_factor", C.c_double), ("energy_pct", C.c_double), ("eta_c", C.c_double),
                 ("eps_exit", C.c_double), ("t_max", C.c_int32), ("exit_enabled", C.c_int32),
-                ("admit_reserve_bytes", C.c_double)]
+                ("admit_reserve_bytes", C.c_double), ("exit_patience", C.c_int32), ("reserved", C.c_int32),
+                ("eta_scale0", C.c_double), ("eta_decay", C.c_double)]
 
 
 class Ticket(C.Structure):

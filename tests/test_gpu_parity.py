@@ -310,3 +310,62 @@ def test_graph_replay_matches_direct_launches():
     assert ia["t"] == ib["t"] == 17 and ia["sd"] == ib["sd"]
     a.close()
     b.close()
+
+
+def test_variable_step_size_matches_oracle():
+    """The tuning notes' variable step size, eta_t = eta scale0 decay^(t-1)
+    (larger steps first): 15 iterates against the oracle with the same schedule."""
+    p = synth.make_problem(MEDIUM, seed=15)
+    op = oracle.Operator.from_problem(p)
+    ini = op.init(p.y, rank=p.rank)
+    it = op.iterate(p.y, ini["U0"], 15, params=oracle.Params(eta_scale0=1.6, eta_decay=0.9), history=True)
+    prm = lrccs.default_params()
+    prm.eta_scale0 = 1.6
+    prm.eta_decay = 0.9
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, params=prm)
+    s.init(*to_dev(p))
+    errs = []
+    for t in range(15):
+        s.iterate(1)
+        U, B = s.factors()
+        errs.append(nrmse((U @ B.T).cpu().numpy().astype(np.complex128), it["X"][t]))
+    assert max(errs) < TOL, errs
+    s.close()
+
+
+def test_robust_exit_matches_oracle():
+    """The tuning notes' robust exit: stop only after 3 consecutive iterations
+    pass the exit test; the GPU stops where the oracle does, on a case whose
+    deciding SD values are at least 5% from the threshold."""
+    p = synth.make_problem(MEDIUM, seed=16)
+    op, ini, it = oracle_run(p, 40)
+    sd = it["sd"] / math.sqrt(p.rank)
+    t_star = next(t for t in range(3, 40) if sd[t - 1] < 0.95 * sd[: t - 1].min())
+    eps = math.sqrt(sd[t_star - 1] * sd[: t_star - 1].min())
+    ref = op.iterate(p.y, ini["U0"], 40, params=oracle.Params(exit_enabled=True, eps_exit=eps, exit_patience=3))
+    close = np.abs(sd[: ref["iters"]] / eps - 1.0) < 0.05
+    if close.any():
+        pytest.skip("an SD value within 5% of the threshold")
+    prm = lrccs.default_params()
+    prm.exit_enabled = 1
+    prm.eps_exit = eps
+    prm.exit_patience = 3
+    s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, params=prm)
+    s.init(*to_dev(p))
+    info = s.iterate(40, info=True)
+    assert info["exited"] == 1 and info["t"] == ref["iters"]
+    s.close()
+
+
+def test_auto_rank_solve_matches_oracle():
+    """rank = 0 end to end: the energy rule picks r, then 10 iterates against
+    the oracle's solve at that rank."""
+    p = synth.make_problem(MEDIUM, seed=17)
+    op = oracle.Operator.from_problem(p)
+    ini = op.init(p.y, rank=0)
+    it = op.iterate(p.y, ini["U0"], 10, history=True)
+    g = gpu_run(p, 10, rank=0)
+    assert g["rank"] == ini["rank"]
+    errs = [nrmse(g["X"][t], it["X"][t]) for t in range(10)]
+    assert max(errs) < TOL, errs
+    g["solver"].close()
