@@ -417,6 +417,19 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
 lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor, double *d_gamma,
                                            void *cuda_stream);
 
+/* Phase timing of the GD/QR kernel (measurement support, like the paper's
+ * per-step timing markers, Sec. V).  enable != 0 allocates a stamp buffer and
+ * makes every later directly launched GD/QR kernel (one-iteration
+ * lrccs_iterate calls; not graph replays) record clock64() at 12 points in
+ * each block: start, inputs staged, gradient and Gram partials done, partials
+ * written, grid barrier 1 passed, totals reduced, barrier 2 passed, the r x r
+ * factors done, U_{t+1} and its partials done, partials written, barrier 3
+ * passed, end.  out (NULL, or 22 doubles) receives, for each of the 11
+ * intervals, the mean and the maximum over the blocks in SM cycles of the last
+ * such launch.  enable == 0 with out == NULL frees the buffer.
+ * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (out requested while off), LRCCS_E_NOMEM. */
+lrccs_status lrccs_gdqr_phases(lrccs_ctx *ctx, int32_t enable, double *out);
+
 /* Test support for the bounded device waits (the paper has no counterpart).
  * With enable != 0 the next directly launched GD/QR kernel of this context (an
  * lrccs_iterate of one iteration, or one with exit_enabled or info) waits at

@@ -82,7 +82,7 @@ static void free_all(lrccs_ctx *c) {
                     c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot, c->d_framek,
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
-                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q};
+                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1320,6 +1320,38 @@ extern "C" lrccs_status lrccs_profile_reset(lrccs_ctx *c) {
         c->prof_ms[k] = 0.0;
     }
     return s;
+}
+
+extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *out) {
+    if (!c) return LRCCS_E_INVALID;
+    const int G = c->gd_grid, NTS = 12;
+    if (out) {
+        if (!c->d_gdts) {
+            set_err(c, "lrccs_gdqr_phases: phase timing is off");
+            return LRCCS_E_STATE;
+        }
+        std::vector<long long> h((size_t)G * NTS);
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpy(h.data(), c->d_gdts, h.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+        for (int i = 0; i + 1 < NTS; ++i) {
+            double sum = 0.0, mx = 0.0;
+            for (int b = 0; b < G; ++b) {
+                const double d = (double)(h[(size_t)b * NTS + i + 1] - h[(size_t)b * NTS + i]);
+                sum += d;
+                mx = d > mx ? d : mx;
+            }
+            out[2 * i] = sum / G;
+            out[2 * i + 1] = mx;
+        }
+    }
+    if (enable && !c->d_gdts) {
+        if (!dalloc(c, &c->d_gdts, (size_t)G * NTS)) return LRCCS_E_NOMEM;
+        CK(cudaMemset(c->d_gdts, 0, (size_t)G * NTS * sizeof(long long)));
+    } else if (!enable && c->d_gdts && !out) {
+        cudaFree(c->d_gdts);
+        c->d_gdts = nullptr;
+    }
+    return LRCCS_OK;
 }
 
 extern "C" lrccs_status lrccs_test_wait_timeout(lrccs_ctx *c, int32_t enable) {

@@ -106,6 +106,7 @@ struct lrccs_ctx {
     int device;        // CUDA device current at lrccs_create
     size_t create_bytes;   // device bytes allocated by lrccs_create
     async_worker *worker;  // started by the first lrccs_track_minibatch_async
+    long long *d_gdts;     // lrccs_gdqr_phases: clock64() stamps of k_gdqr's blocks (NULL: off)
     std::string err;
 
     // geometry / sampling

@@ -50,9 +50,18 @@ struct GdArgs {
     int n, r, q, zs, chunk, resident, mode;
     double eta_c;
     double eta_scale0, eta_decay;   // variable step size: eta_t = eta eta_scale0 eta_decay^k
+    long long *ts;             // NULL, or GD_NTS clock64() stamps per block (phase timing)
     unsigned int spin_limit;   // polls before a grid barrier gives up (2^24 normally)
     unsigned int bar_skew;     // extra arrivals a barrier waits for (0; 1 only for the timeout test)
 };
+
+// Phase timing (measurement support): thread 0 of every block stamps clock64()
+// at GD_NTS points of the kernel when a.ts is set.
+#define GD_NTS 12
+#define GD_TS(i)                                                                    \
+    do {                                                                            \
+        if (a.ts && threadIdx.x == 0) a.ts[(size_t)blockIdx.x * GD_NTS + (i)] = clock64(); \
+    } while (0)
 
 // ---------------------------------------------------------------- grid-wide steps
 
@@ -357,6 +366,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) acc[u][m] = make_float2(0.f, 0.f);
     }
+    GD_TS(0);
     if (iter)
         for (int e = t; e < q * r; e += NTG) cp_async8(sB + e, a.B + e);
     for (int c0 = i0; c0 < i1; c0 += chunk) {
@@ -372,6 +382,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         cp_async_commit();
         cp_async_wait();
         __syncthreads();
+        if (c0 == i0) GD_TS(1);
         if (iter) {
             // grad = Gk - Z B^H.  Thread = (pixel pair pp, part kq of the k range,
             // NQ = NTG / 128 parts); the parts are subtracted from Gk in the fixed
@@ -426,6 +437,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         for (int u = 0; u < 2; ++u)
             if (sl1[u] < S1) tile_accumulate(g1[u], acc[u], sl1[u], S1, cn);
     }
+    GD_TS(2);
     // partial row: [grad^H grad pairs (np) | U^H grad (rr) | U^H U pairs (np)], init: [U+^H U+ pairs]
     tiles_write(acc, T1, S1, s_w, chunk * r, s_red2, a.part, len1, [&](int w, int m) {
         int kind, A, Bt;
@@ -436,9 +448,13 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         if (x > y) return -1;
         return (kind == 2 && iter ? np + rr : 0) + pair_index(x, y, r);
     });
+    GD_TS(3);
     grid_sync(a.bar, 1, a.status, a.spin_limit, a.bar_skew);
+    GD_TS(4);
     grid_reduce(a.part, len1, a.tot);
+    GD_TS(5);
     grid_sync(a.bar, 2, a.status, a.spin_limit, a.bar_skew);
+    GD_TS(6);
     for (int e = t; e < len1; e += NTG) {
         const double2 v = __ldcg(a.tot + e);
         s_tot[e] = make_float2((float)v.x, (float)v.y);
@@ -505,6 +521,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         __syncthreads();
     }
     block_rinv<R>(sL, sinv, sX, sR);
+    GD_TS(7);
     const float etaf = iter ? s_eta : 0.f;
 
     // ------------------------------------------------ phase 2: U_{t+1} = (U - eta grad) R1^{-1}
@@ -572,6 +589,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             }
         }
     }
+    GD_TS(8);
     // partial row: [U_t^H U_{t+1} (rr, x r + y) | h (q r, k r + l)]; slices summed in
     // order, V values per thread per round (s_w and s_z are free after the last chunk)
     {
@@ -605,8 +623,11 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             }
         }
     }
+    GD_TS(9);
     grid_sync(a.bar, 3, a.status, a.spin_limit, a.bar_skew);
+    GD_TS(10);
     grid_reduce(a.part, len2, a.tot);
+    GD_TS(11);
     // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2, and
     // the barrier counters back to zero (every block is past its last barrier)
     __syncthreads();
@@ -697,6 +718,7 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.eta_decay = c->prm.eta_decay > 0.0 ? c->prm.eta_decay : 1.0;
     a.spin_limit = 1u << 24;
     a.bar_skew = 0;
+    a.ts = (mode == 1 && !c->capturing) ? c->d_gdts : nullptr;
     if (c->test_timeout && !c->capturing) {   // lrccs_test_wait_timeout: this launch only
         a.spin_limit = 1u << 16;
         a.bar_skew = 1;

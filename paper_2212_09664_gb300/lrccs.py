@@ -73,6 +73,7 @@ _sig = {
     "lrccs_get_state": (_st, [_vp, _vp, C.POINTER(C.c_size_t)]),
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
+    "lrccs_gdqr_phases": (_st, [_vp, C.c_int32, C.POINTER(C.c_double)]),
     "lrccs_context_bytes": (_st, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lrccs_track_minibatch_async": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.c_void_p]),
     "lrccs_ticket_query": (_st, [_vp, C.c_void_p, C.POINTER(C.c_int32)]),
@@ -265,6 +266,13 @@ def lrccs_get_state(ctx) -> bytes:
 
 def lrccs_set_state(ctx, state: bytes):
     _check(ctx, _lib.lrccs_set_state(ctx, state, len(state)))
+
+
+def lrccs_gdqr_phases(ctx, enable: bool = True, read: bool = False):
+    """Phase timing of the GD/QR kernel: returns [(mean, max) cycles] per interval when read."""
+    out = (C.c_double * 22)() if read else None
+    _check(ctx, _lib.lrccs_gdqr_phases(ctx, 1 if enable else 0, out))
+    return [(out[2 * i], out[2 * i + 1]) for i in range(11)] if read else None
 
 
 def lrccs_test_wait_timeout(ctx, enable: bool = True):
