@@ -82,7 +82,7 @@ static void free_all(lrccs_ctx *c) {
                     c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot, c->d_framek,
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
-                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts};
+                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -329,7 +329,8 @@ static lrccs_status ensure_general_buffers(lrccs_ctx *c) {
                     dalloc(c, &c->d_urow, 2 * ny) && dalloc(c, &c->d_uptr, ny + 1) &&
                     dalloc(c, &c->d_ufrow, ny + 1) && dalloc(c, &c->d_upos, n) && dalloc(c, &c->d_uidx, n) &&
                     dalloc(c, &c->d_ufptr, n + 1) && dalloc(c, &c->d_uflist, q * n) && dalloc(c, &c->d_fu, q * n) &&
-                    dalloc(c, &c->d_FU, (size_t)c->nc * n * c->rmax) && dalloc(c, &c->d_Pu, n * npm);
+                    dalloc(c, &c->d_FU, (size_t)c->nc * n * c->rmax) && dalloc(c, &c->d_Pu, n * npm) &&
+                    dalloc(c, &c->d_fpart, frame_gram_part_count(c->q, c->rmax));
     if (!ok) return LRCCS_E_NOMEM;
     c->gen_cap_q = q;
     return LRCCS_OK;
@@ -373,8 +374,9 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     } else {
         CK(launch_fill_lines(c));
     }
-    // init row pass: full rows (nx) for every (frame row, coil), plain and truncated
-    const size_t need = (size_t)2 * c->nc * c->n_lines * c->nx;
+    // line masks' init row pass: full rows (nx) for every (frame row, coil), plain
+    // and truncated (the general masks' init needs no such buffer)
+    const size_t need = c->general ? 0 : (size_t)2 * c->nc * c->n_lines * c->nx;
     if (need > c->T_cap) {
         cudaFree(c->d_T);
         c->d_T = nullptr;
@@ -1227,7 +1229,7 @@ extern "C" lrccs_status lrccs_get_buffer(lrccs_ctx *c, lrccs_buffer which, void 
 const char *const kKernelNames[KID_COUNT] = {
     "k_rowcount", "k_structure", "k_fill_idx", "k_energy", "k_init_rows", "k_init_cols", "k_gram_x0",
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
-    "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_rows_gen",
+    "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
     "k_mec_elem", "k_mec_tdft"};
 

@@ -44,7 +44,7 @@ enum {
     KID_EIG, KID_U0, KID_GDQR, KID_FWD_COLS, KID_ROW_GRAM, KID_SOLVE, KID_ROW_W, KID_ADJ_COLS,
     KID_IMAGES, KID_CG_INIT, KID_CG_STEP, KID_MEAN_RESID,
     // general (2D) masks
-    KID_UNION, KID_FILL_GEN, KID_INIT_ROWS_GEN, KID_FWD_ROWS, KID_SAMPLE_GRAM, KID_SOLVE_GEN, KID_SAMPLE_W,
+    KID_UNION, KID_FILL_GEN, KID_INIT_GEN, KID_FWD_ROWS, KID_SAMPLE_GRAM, KID_SOLVE_GEN, KID_SAMPLE_W,
     KID_ADJ_ROWS, KID_MEAN_RESID_GEN,
     // model-error correction (Alg. 3) and online tracking (Alg. 5)
     KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT, KID_COUNT
@@ -164,6 +164,7 @@ struct lrccs_ctx {
     int32_t *d_fu;               // sum m_k union index of every frame sample (frame-ordered)
     float2 *d_FU;                // nc * n_u * rmax  F(d_j o U) at the union points (FU[j][u][l])
     float2 *d_Pu;                // n_u * npairs      coil-summed Gram of every union point
+    double *d_fpart;             // q * 8 chunks * 2 npairs  per-frame Gram partial sums (FP64)
 
     // model-error correction (Alg. 3): frames in chunks of mec_w = rank_max
     // columns, vectors V[c][i][l] (frame c mec_w + l)
@@ -186,7 +187,7 @@ cudaError_t launch_compact(lrccs_ctx *c, const uint8_t *d_mask, const int64_t *d
 cudaError_t launch_fill_lines(lrccs_ctx *c);
 // general (2D) masks (kernels_general.cu)
 cudaError_t launch_compact_general(lrccs_ctx *c, const uint8_t *d_mask);
-cudaError_t launch_init_rows_general(lrccs_ctx *c, const float2 *d_y);
+cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y);   // Z and X0 in one pass (general masks)
 cudaError_t launch_iteration_general_front(lrccs_ctx *c);   // forward rows + sample Grams + B-step
 cudaError_t launch_iteration_general_back(lrccs_ctx *c);    // W per sample + inverse rows
 cudaError_t launch_fwd_rows(lrccs_ctx *c);
@@ -207,6 +208,7 @@ cudaError_t launch_tdft_fwd(lrccs_ctx *c, const float2 *E, const float2 *S0, con
                             float2 *M, double *out);
 cudaError_t launch_tdft_inv(lrccs_ctx *c, const float2 *M, float omega, float2 *E);
 size_t mec_scal_count(int n, int q, int w);
+size_t frame_gram_part_count(int q, int rmax);   // doubles of d_fpart
 cudaError_t launch_bstep(lrccs_ctx *c);   // B-step only (forward transforms, Grams, solve) at the current U
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);

@@ -151,77 +151,26 @@ static __device__ void stage_rows(float2 *dst, int ds, const float2 *src, int ss
     }
 }
 
-// G1 = L L^H (in place, Hermitian r x r, FP32) with all threads of the block:
-// step c scales column c, then the trailing entries (i, j), c < j <= i, are
-// updated in parallel (entry e of the trailing block of step c is (c+1+ti,
-// c+1+tj) with e = ti (ti+1)/2 + tj).  The strict upper triangle is zeroed and
-// invd[c] = 1 / L[c][c].  Returns false (every thread) if a pivot is not
-// positive.  Inside this kernel, block-wide steps run several times faster than
-// the same factorisation done by a single warp.
+// Rinv = (L^H)^{-1} for the lower-triangular L of warp_chol32 (row-major R x R,
+// invd = 1 / diag), by one warp: lane j forms column j of X = L^{-1} by
+// forward substitution in registers (L read by broadcast), then row j of
+// Rinv = X^H (upper triangular).
 template <int R>
-static __device__ bool block_chol(float2 *A, float *invd) {
-    const int t = threadIdx.x;
-#pragma unroll 1
-    for (int c = 0; c < R; ++c) {
-        const float d = A[c * R + c].x;
-        if (!(d > 0.f)) return false;
-        const float is = rsqrtf(d);
-        if (t > c && t < R) A[t * R + c] = cscale(A[t * R + c], is);
-        __syncthreads();
-        if (t == c) {
-            A[c * R + c] = make_float2(d * is, 0.f);
-            invd[c] = is;
-        }
-        const int Rt = R - c - 1, m = Rt * (Rt + 1) / 2;
-        if (t < m) {
-            int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-            while (ti * (ti + 1) / 2 > t) --ti;
-            const int i = c + 1 + ti, j = c + 1 + (t - ti * (ti + 1) / 2);
-            const float2 li = A[i * R + c], lj = A[j * R + c];
-            float2 v = A[i * R + j];
-            v.x -= li.x * lj.x + li.y * lj.y;
-            v.y -= li.y * lj.x - li.x * lj.y;
-            A[i * R + j] = v;
-        }
-        __syncthreads();
+static __device__ void warp_rinv(const float2 *L, const float *invd, float2 *Rinv) {
+    const int j = threadIdx.x & 31;
+    float2 x[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        float2 acc = make_float2(i == j ? 1.f : 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < i; ++m) acc = csub(acc, cmul(L[i * R + m], x[m]));
+        x[i] = cscale(acc, invd[i]);   // zero for i < j
     }
-    if (t < R * R && (t % R) > (t / R)) A[t] = make_float2(0.f, 0.f);
-    __syncthreads();
-    return true;
-}
-
-// Rinv = (L^H)^{-1} (upper triangular) for the factor of block_chol: rows of
-// X = L^{-1} right-looking, all threads: after row c is final,
-// X[i][j] -= L[i][c] X[c][j] for every later row i and j <= c in parallel.
-// Stored as Rinv[j][i] = conj(X[i][j]).
-template <int R>
-static __device__ void block_rinv(const float2 *L, const float *invd, float2 *X, float2 *Rinv) {
-    const int t = threadIdx.x;
-    if (t < R * R) X[t] = make_float2((t / R) == (t % R) ? 1.f : 0.f, 0.f);
-    __syncthreads();
-#pragma unroll 1
-    for (int c = 0; c < R; ++c) {
-        // row c final: X[c][j] *= invd[c] (j <= c); then update rows i > c
-        const int i = c + 1 + t / (c + 1), j = t % (c + 1);
-        float2 xcj = make_float2(0.f, 0.f);
-        if (t < (R - c - 1) * (c + 1) || t <= c) xcj = cscale(X[c * R + (t <= c ? t : j)], invd[c]);
-        __syncthreads();
-        if (t <= c) X[c * R + t] = xcj;
-        if (t < (R - c - 1) * (c + 1)) {
-            const float2 l = L[i * R + c];
-            float2 v = X[i * R + j];
-            v.x -= l.x * xcj.x - l.y * xcj.y;
-            v.y -= l.x * xcj.y + l.y * xcj.x;
-            X[i * R + j] = v;
-        }
-        __syncthreads();
+    if (j < R) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) Rinv[j * R + i] = i >= j ? cconj(x[i]) : make_float2(0.f, 0.f);
     }
-    if (t < R * R) {
-        const int a = t / R, b = t % R;   // Rinv[a][b] = conj(X[b][a]) for a <= b
-        Rinv[t] = a <= b ? cconj(X[b * R + a]) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
+    __syncwarp();
 }
 
 // 2 x 2 tile of a cross-Gram: acc[2 i + j] += sum_ii conj(X[ii][x_i]) Y[ii][y_j].
@@ -306,7 +255,6 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     __shared__ __align__(16) float2 sB[QMAXC * R];
     __shared__ float2 sL[R * R];
     __shared__ float2 sR[R * R];
-    __shared__ float2 sX[R * R];
     __shared__ float sinv[R];
     __shared__ float2 s_tot[2 * (R * (R + 1) / 2) + R * R];
     __shared__ float2 s_red2[2 * NTG];
@@ -513,14 +461,18 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         }
     }
     __syncthreads();
-    if (!block_chol<R>(sL, sinv)) {
-        if (t == 0 && blockIdx.x == 0) atomicOr(a.status, (unsigned)ST_NOT_SPD_QR);
-        __syncthreads();
-        if (t < rr) sL[t] = make_float2(t / r == t % r ? 1.f : 0.f, 0.f);
-        if (t < r) sinv[t] = 1.f;
-        __syncthreads();
+    // G1 = L L^H and R1^{-1} = (L^H)^{-1} by the first warp in registers (the
+    // other warps wait at the barrier below)
+    if (t < 32) {
+        if (!warp_chol32<R>(sL, R, sinv)) {
+            if (t == 0 && blockIdx.x == 0) atomicOr(a.status, (unsigned)ST_NOT_SPD_QR);
+            for (int e = t; e < rr; e += 32) sL[e] = make_float2(e / r == e % r ? 1.f : 0.f, 0.f);
+            if (t < r) sinv[t] = 1.f;
+            __syncwarp();
+        }
+        warp_rinv<R>(sL, sinv, sR);
     }
-    block_rinv<R>(sL, sinv, sX, sR);
+    __syncthreads();
     GD_TS(7);
     const float etaf = iter ? s_eta : 0.f;
 

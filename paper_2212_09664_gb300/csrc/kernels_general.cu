@@ -20,8 +20,8 @@
 //   E  k_adj_rows     : scatter a row's union points, F_x^H           -> T[j][ky][x][l]
 //   F  k_adj_cols     : F_y^H and the conj(d_j) coil sum              -> Gk
 //   G  k_gdqr         : gradient, GD step, QR                          (kernels_gd.cu)
-// and the spectral initialisation's row pass k_init_rows_gen, which scatters
-// each frame row's samples before its inverse x transform.
+// and the spectral initialisation's fused pass k_init_gen (Z and X0: direct
+// inverse DFT along kx of each frame row's few samples, then the column FFTs).
 #include <math.h>
 
 #include "common.cuh"
@@ -182,66 +182,102 @@ cudaError_t launch_compact_general(lrccs_ctx *c, const uint8_t *d_mask) {
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- init: row pass
+// ---------------------------------------------------------------- init: fused pass
 
-// Block (4 consecutive frame rows g, coil j): scatter each row's samples (the
-// plain ones and the truncated ones, |y|^2 <= gamma) into zero rows, inverse
-// DFT along kx, and store them in the layout the column pass reads:
-// T0[((nc lineptr[k] + j L_k + li) nx + x) 2 + {plain, truncated}].
-template <int PX>
-__global__ void __launch_bounds__(256) k_init_rows_gen(
-    const float2 *__restrict__ y, const int32_t *__restrict__ idx, const int32_t *__restrict__ framerows,
-    const int32_t *__restrict__ framek, const int32_t *__restrict__ lineptr, const int32_t *__restrict__ rowoff,
-    const int32_t *__restrict__ rowcnt, const int32_t *__restrict__ fpk, const int32_t *__restrict__ mks,
-    const double *__restrict__ scal, int n_lines, int ny, int nc, float2 *__restrict__ T0,
-    const float2 *__restrict__ g_tw, float scale) {
-    constexpr int N = 32 * PX;
-    constexpr int ROWS = 4, TPR = 2 * ROWS + 1;
-    __shared__ float2 s_tw[N];
-    __shared__ float2 tile[N * TPR];
-    load_twiddles(s_tw, g_tw, N);
-    const int g0 = blockIdx.x * ROWS, j = blockIdx.y;
+// Z[:, k] = A_k^H y_k and X0[:, k] = A_k^H y_k,tnc / sqrt(m_k mbar) for general
+// masks in one pass, block (tile of TXG columns, frame k).  For every coil the
+// inverse DFT along kx of each frame row is evaluated directly from the row's
+// few samples at the tile's columns (T[ky][x] = sum_s y_s e^{+2 pi i kx_s x / nx}
+// / sqrt(nx), plain and truncated), then the column tile is transformed back
+// along ky and multiplied by conj(d_j) into the coil sum.  Nothing the size of
+// full k-space rows goes through memory.
+#define TXG 16
+template <int P>
+__global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, const int32_t *__restrict__ idx,
+                                                  const int32_t *__restrict__ framerows,
+                                                  const int32_t *__restrict__ lineptr,
+                                                  const int32_t *__restrict__ rowoff, const int32_t *__restrict__ rowcnt,
+                                                  const int32_t *__restrict__ fpk, const int32_t *__restrict__ mks,
+                                                  const float2 *__restrict__ smaps, const double *__restrict__ scal,
+                                                  float2 *__restrict__ Z, float2 *__restrict__ X0, int nx, int q,
+                                                  int nc, const float2 *__restrict__ g_twy,
+                                                  const float2 *__restrict__ g_twx, float sy, float sx) {
+    constexpr int NY = 32 * P;
+    constexpr int TP = 2 * TXG + 1;
+    constexpr int ACC = (NY * 2 * TXG + 255) / 256;
+    extern __shared__ __align__(16) float2 smem[];
+    float2 *tile = smem;                  // NY * TP
+    float2 *s_S = tile + NY * TP;         // NY * TXG
+    float2 *s_twy = s_S + NY * TXG;       // NY
+    float2 *s_twx = s_twy + NY;           // nx
+    const int k = blockIdx.y, x0 = blockIdx.x * TXG;
+    const int n = NY * nx;
+    load_twiddles(s_twy, g_twy, NY);
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) s_twx[t] = g_twx[t];
+    const int lp = lineptr[k], L = lineptr[k + 1] - lp;
+    const int f0 = fpk[k], mk = mks[k];
     const double gam = scal[SC_GAMMA];
-    for (int e = threadIdx.x; e < N * TPR; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int row = 0; row < ROWS; ++row) {
-        const int g = g0 + row;
-        if (g >= n_lines) break;   // the same for every thread
-        const int k = framek[g], ky = framerows[g];
-        const int w = k * ny + ky;
-        const int off = rowoff[w], cnt = rowcnt[w], f0 = fpk[k];
-        const int64_t ybase = (int64_t)nc * f0 + (int64_t)j * mks[k] + (off - f0);
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int kx = idx[off + t] - ky * N;
-            const float2 a = y[ybase + t];
-            tile[kx * TPR + 2 * row] = a;
-            tile[kx * TPR + 2 * row + 1] = abs2_rn(a) > gam ? make_float2(0.f, 0.f) : a;
+    float2 acc[ACC];
+#pragma unroll
+    for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int j = 0; j < nc; ++j) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NY * TP; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < NY * TXG; e += blockDim.x)
+            s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXG) * nx + x0 + (e % TXG)];
+        __syncthreads();
+        const int64_t yb = (int64_t)nc * f0 + (int64_t)j * mk;   // sample f0 + s of coil j at y[yb + s]
+        for (int e = threadIdx.x; e < L * TXG; e += blockDim.x) {
+            const int li = e / TXG, xx = e - li * TXG, x = x0 + xx;
+            const int ky = framerows[lp + li];
+            const int off = rowoff[k * NY + ky], cnt = rowcnt[k * NY + ky];
+            float2 vp = make_float2(0.f, 0.f), vt = make_float2(0.f, 0.f);
+            for (int s = off; s < off + cnt; ++s) {
+                const float2 a = __ldg(y + yb + (s - f0));
+                const int kx = __ldg(idx + s) - ky * nx;
+                const float2 w = cconj(s_twx[(kx * x) % nx]);   // e^{+2 pi i kx x / nx}
+                cfma(vp, a, w);
+                if (!(abs2_rn(a) > gam)) cfma(vt, a, w);
+            }
+            tile[ky * TP + 2 * xx] = cscale(vp, sx);
+            tile[ky * TP + 2 * xx + 1] = cscale(vt, sx);
+        }
+        __syncthreads();
+        fft::tile_dft<NY, true>(tile, TP, 2 * TXG, s_twy, sy);
+#pragma unroll
+        for (int u = 0; u < ACC; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            if (e < NY * 2 * TXG) {
+                const int yy = e / (2 * TXG), cc = e % (2 * TXG);
+                cfmac(acc[u], s_S[yy * TXG + (cc >> 1)], tile[yy * TP + cc]);
+            }
         }
     }
-    __syncthreads();
-    fft::tile_dft<N, true>(tile, TPR, 2 * ROWS, s_tw, scale);
-    for (int e = threadIdx.x; e < ROWS * 2 * N; e += blockDim.x) {
-        const int row = e / (2 * N), rem = e - row * 2 * N, x = rem >> 1, ch = rem & 1;
-        const int g = g0 + row;
-        if (g < n_lines) {
-            const int k = framek[g];
-            const int lp = lineptr[k], L = lineptr[k + 1] - lp, li = g - lp;
-            const int64_t trow = (int64_t)nc * lp + (int64_t)j * L + li;
-            T0[trow * N * 2 + rem] = tile[x * TPR + 2 * row + ch];
+    const double mbar = scal[SC_MBAR];
+    const float xs = (mk > 0) ? (float)(1.0 / sqrt((double)mk * mbar)) : 0.f;
+#pragma unroll
+    for (int u = 0; u < ACC; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        if (e < NY * 2 * TXG) {
+            const int yy = e / (2 * TXG), cc = e % (2 * TXG);
+            const size_t i = (size_t)yy * nx + x0 + (cc >> 1);
+            if ((cc & 1) == 0) Z[i * q + k] = acc[u];
+            else X0[i * q + k] = cscale(acc[u], xs);
         }
     }
 }
 
-cudaError_t launch_init_rows_general(lrccs_ctx *c, const float2 *d_y) {
-    if (c->n_lines <= 0) return cudaSuccess;
-    const float sx = (float)(1.0 / sqrt((double)c->nx));
-    dim3 grid((c->n_lines + 3) / 4, c->nc);
-    DISPATCH_P(c->px, {
-        prof_begin(c, KID_INIT_ROWS_GEN);
-        k_init_rows_gen<P_><<<grid, 256, 0, c->stream>>>(d_y, c->d_idx, c->d_framerows, c->d_framek, c->d_lineptr,
-                                                         c->d_rowoff, c->d_rowcnt, c->d_fpk, c->d_mks, c->d_scal,
-                                                         c->n_lines, c->ny, c->nc, c->d_T, c->d_twx, sx);
-        prof_end(c, KID_INIT_ROWS_GEN);
+cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y) {
+    const float sx = (float)(1.0 / sqrt((double)c->nx)), sy = (float)(1.0 / sqrt((double)c->ny));
+    const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->ny * TXG + c->ny + c->nx) * sizeof(float2);
+    dim3 grid(c->nx / TXG, c->q);
+    DISPATCH_P(c->py, {
+        prof_begin(c, KID_INIT_GEN);
+        k_init_gen<P_><<<grid, 256, smem, c->stream>>>(d_y, c->d_idx, c->d_framerows, c->d_lineptr, c->d_rowoff,
+                                                       c->d_rowcnt, c->d_fpk, c->d_mks, c->d_smaps, c->d_scal,
+                                                       c->d_Z, c->d_X0, c->nx, c->q, c->nc, c->d_twy, c->d_twx, sy,
+                                                       sx);
+        prof_end(c, KID_INIT_GEN);
     });
     return cudaGetLastError();
 }
@@ -529,5 +565,7 @@ cudaError_t configure_kernels_general(int max_smem) {
     SET_SMEM(k_adj_rows<1>); SET_SMEM(k_adj_rows<2>); SET_SMEM(k_adj_rows<3>); SET_SMEM(k_adj_rows<4>);
     SET_SMEM(k_adj_rows<5>); SET_SMEM(k_adj_rows<6>); SET_SMEM(k_adj_rows<7>); SET_SMEM(k_adj_rows<8>);
     for (int i = 0; i < RMAXC; ++i) SET_SMEM(kSampleW[i]);
+    SET_SMEM(k_init_gen<1>); SET_SMEM(k_init_gen<2>); SET_SMEM(k_init_gen<3>); SET_SMEM(k_init_gen<4>);
+    SET_SMEM(k_init_gen<5>); SET_SMEM(k_init_gen<6>); SET_SMEM(k_init_gen<7>); SET_SMEM(k_init_gen<8>);
     return cudaSuccess;
 }

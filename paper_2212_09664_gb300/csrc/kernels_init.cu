@@ -329,10 +329,8 @@ cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const float sy = (float)(1.0 / sqrt((double)c->ny));
     const unsigned rb = (unsigned)((total_rows + 3) / 4);
-    if (c->general) {   // frame rows hold scattered samples: scatter, then the row transforms
-        cudaError_t eg = launch_init_rows_general(c, d_y);
-        if (eg != cudaSuccess) return eg;
-    } else if (total_rows > 0) {
+    if (c->general) return launch_init_general(c, d_y);   // frame rows hold scattered samples: one fused pass
+    if (total_rows > 0) {
         DISPATCH_P(c->px, {
             prof_begin(c, KID_INIT_ROWS);
             k_init_rows<P_><<<rb, 256, 0, c->stream>>>(d_y, c->d_T, total_rows, c->d_scal, c->d_twx, sx);

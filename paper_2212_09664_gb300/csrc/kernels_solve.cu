@@ -59,19 +59,39 @@ __global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, c
 }
 
 // General masks: G_k = sum over the frame's samples s of the point Grams
-// P_{u(s)} (u(s) = fu[s], the union index of sample s).
+// P_{u(s)} (u(s) = fu[s], the union index of sample s).  A frame holds
+// thousands of samples, so the sum is split: block (k, c) sums chunk c of
+// GEN_NCH of the frame's samples (FP64 pairs), and k_solve_gen adds the
+// chunks in order and solves.
+#define GEN_NCH 8
 template <int R>
-__global__ void __launch_bounds__(NT) k_solve_gen(const float2 *__restrict__ Pu, const double2 *__restrict__ htot,
-                                                  const int32_t *__restrict__ fpk, const int32_t *__restrict__ fu,
-                                                  float2 *__restrict__ B, unsigned int *status) {
+__global__ void __launch_bounds__(NT) k_frame_gram_gen(const float2 *__restrict__ Pu, const int32_t *__restrict__ fpk,
+                                                       const int32_t *__restrict__ fu, double *__restrict__ part) {
+    constexpr int np = R * (R + 1) / 2;
+    const int k = blockIdx.x, c = blockIdx.y;
+    const int f0 = fpk[k], m = fpk[k + 1] - f0;
+    const int a0 = (int)((long long)m * c / GEN_NCH), a1 = (int)((long long)m * (c + 1) / GEN_NCH);
+    const int32_t *fk = fu + f0 + a0;
+    block_sum(np, a1 - a0, part + ((size_t)k * GEN_NCH + c) * 2 * np,
+              [=](int p, int i) { return __ldg(Pu + (size_t)__ldg(fk + i) * np + p); });
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT) k_solve_gen(const double *__restrict__ part, const double2 *__restrict__ htot,
+                                                  const int32_t *__restrict__ fpk, float2 *__restrict__ B,
+                                                  unsigned int *status) {
     constexpr int np = R * (R + 1) / 2;
     __shared__ double sP[2 * np];
     __shared__ float2 sG[R * R];
     __shared__ float sinv[R];
     const int k = blockIdx.x;
-    const int f0 = fpk[k], m = fpk[k + 1] - f0;
-    const int32_t *fk = fu + f0;
-    block_sum(np, m, sP, [=](int p, int i) { return __ldg(Pu + (size_t)__ldg(fk + i) * np + p); });
+    const int m = fpk[k + 1] - fpk[k];
+    for (int e = threadIdx.x; e < 2 * np; e += blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < GEN_NCH; ++c) acc += part[((size_t)k * GEN_NCH + c) * 2 * np + e];
+        sP[e] = acc;
+    }
+    __syncthreads();
     solve_frame<R>(sP, sG, sinv, m > 0, htot, k, B, status);
 }
 
@@ -82,18 +102,22 @@ static const solve_kernel_t kSolve[RMAXC] = {k_solve<1>,  k_solve<2>,  k_solve<3
                                              k_solve<9>,  k_solve<10>, k_solve<11>, k_solve<12>,
                                              k_solve<13>, k_solve<14>, k_solve<15>, k_solve<16>};
 
-typedef void (*solve_gen_t)(const float2 *, const double2 *, const int32_t *, const int32_t *, float2 *,
-                            unsigned int *);
-static const solve_gen_t kSolveGen[RMAXC] = {k_solve_gen<1>,  k_solve_gen<2>,  k_solve_gen<3>,  k_solve_gen<4>,
-                                             k_solve_gen<5>,  k_solve_gen<6>,  k_solve_gen<7>,  k_solve_gen<8>,
-                                             k_solve_gen<9>,  k_solve_gen<10>, k_solve_gen<11>, k_solve_gen<12>,
-                                             k_solve_gen<13>, k_solve_gen<14>, k_solve_gen<15>, k_solve_gen<16>};
+typedef void (*fgram_t)(const float2 *, const int32_t *, const int32_t *, double *);
+typedef void (*solve_gen_t)(const double *, const double2 *, const int32_t *, float2 *, unsigned int *);
+#define RANK_TABLE(K) {K<1>, K<2>, K<3>, K<4>, K<5>, K<6>, K<7>, K<8>, K<9>, K<10>, K<11>, K<12>, K<13>, K<14>, K<15>, K<16>}
+static const fgram_t kFrameGramGen[RMAXC] = RANK_TABLE(k_frame_gram_gen);
+static const solve_gen_t kSolveGen[RMAXC] = RANK_TABLE(k_solve_gen);
+
+size_t frame_gram_part_count(int q, int rmax) { return (size_t)q * GEN_NCH * rmax * (rmax + 1); }
 
 cudaError_t launch_solve(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
     if (c->general) {
         prof_begin(c, KID_SOLVE_GEN);
-        kSolveGen[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_Pu, c->d_tot, c->d_fpk, c->d_fu, c->d_B, c->d_status);
+        kFrameGramGen[c->r - 1]<<<dim3(c->q, GEN_NCH), NT, 0, c->stream>>>(c->d_Pu, c->d_fpk, c->d_fu, c->d_fpart);
+        prof_end(c, KID_SOLVE_GEN);
+        prof_begin(c, KID_SOLVE_GEN);
+        kSolveGen[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_fpart, c->d_tot, c->d_fpk, c->d_B, c->d_status);
         prof_end(c, KID_SOLVE_GEN);
         return cudaGetLastError();
     }
