@@ -82,7 +82,8 @@ static void free_all(lrccs_ctx *c) {
                     c->d_B, c->d_P, c->d_gpart, c->d_sigma, c->d_gram, c->d_V, c->d_tot, c->d_framek,
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
-                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart};
+                    c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart,
+                    c->d_tflag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -367,6 +368,14 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     if (c->general) {
         s = ensure_general_buffers(c);
         if (s != LRCCS_OK) return s;
+        const size_t nflag = (size_t)c->nc * c->total;
+        if (nflag > c->tflag_cap) {
+            if (c->d_tflag) cudaFree(c->d_tflag);
+            c->d_tflag = nullptr;
+            c->tflag_cap = 0;
+            if (!dalloc(c, &c->d_tflag, nflag)) return LRCCS_E_NOMEM;
+            c->tflag_cap = nflag;
+        }
         CK(launch_compact_general(c, d_mask));
         CK(cudaMemcpyAsync(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));

@@ -165,6 +165,8 @@ struct lrccs_ctx {
     float2 *d_FU;                // nc * n_u * rmax  F(d_j o U) at the union points (FU[j][u][l])
     float2 *d_Pu;                // n_u * npairs      coil-summed Gram of every union point
     double *d_fpart;             // q * 8 chunks * 2 npairs  per-frame Gram partial sums (FP64)
+    uint8_t *d_tflag;            // C sum_k m_k  truncation flags of the init (capacity tflag_cap)
+    size_t tflag_cap;
 
     // model-error correction (Alg. 3): frames in chunks of mec_w = rank_max
     // columns, vectors V[c][i][l] (frame c mec_w + l)

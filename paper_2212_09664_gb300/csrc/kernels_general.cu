@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
                                                   const int32_t *__restrict__ rowoff, const int32_t *__restrict__ rowcnt,
                                                   const int32_t *__restrict__ fpk, const int32_t *__restrict__ mks,
                                                   const float2 *__restrict__ smaps, const double *__restrict__ scal,
-                                                  float2 *__restrict__ Z, float2 *__restrict__ X0, int nx, int q,
-                                                  int nc, const float2 *__restrict__ g_twy,
-                                                  const float2 *__restrict__ g_twx, float sy, float sx) {
+                                                  const uint8_t *__restrict__ tflag, float2 *__restrict__ Z,
+                                                  float2 *__restrict__ X0, int nx, int q, int nc,
+                                                  const float2 *__restrict__ g_twy, const float2 *__restrict__ g_twx,
+                                                  float sy, float sx, float inv_nx) {
     constexpr int NY = 32 * P;
     constexpr int TP = 2 * TXG + 1;
     constexpr int ACC = (NY * 2 * TXG + 255) / 256;
@@ -216,7 +217,6 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
     for (int t = threadIdx.x; t < nx; t += blockDim.x) s_twx[t] = g_twx[t];
     const int lp = lineptr[k], L = lineptr[k + 1] - lp;
     const int f0 = fpk[k], mk = mks[k];
-    const double gam = scal[SC_GAMMA];
     float2 acc[ACC];
 #pragma unroll
     for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
@@ -235,9 +235,14 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
             for (int s = off; s < off + cnt; ++s) {
                 const float2 a = __ldg(y + yb + (s - f0));
                 const int kx = __ldg(idx + s) - ky * nx;
-                const float2 w = cconj(s_twx[(kx * x) % nx]);   // e^{+2 pi i kx x / nx}
+                // (kx x) mod nx without an integer division: kx x < 2^16 is exact in FP32
+                const int p = kx * x;
+                int m = p - nx * (int)((float)p * inv_nx);
+                m += m < 0 ? nx : 0;
+                m -= m >= nx ? nx : 0;
+                const float2 w = cconj(s_twx[m]);   // e^{+2 pi i kx x / nx}
                 cfma(vp, a, w);
-                if (!(abs2_rn(a) > gam)) cfma(vt, a, w);
+                if (!tflag[yb + (s - f0)]) cfma(vt, a, w);   // kept by the truncation (|y|^2 <= gamma)
             }
             tile[ky * TP + 2 * xx] = cscale(vp, sx);
             tile[ky * TP + 2 * xx + 1] = cscale(vt, sx);
@@ -267,16 +272,28 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
     }
 }
 
+// The truncation decision of every measured entry, |y|^2 > gamma (FP64 squares,
+// as in the line path), once per entry: 1 = dropped from X0.
+__global__ void k_trunc_flags(const float2 *__restrict__ y, int64_t count, const double *__restrict__ scal,
+                              uint8_t *__restrict__ flag) {
+    const double gam = scal[SC_GAMMA];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = abs2_rn(y[e]) > gam ? 1 : 0;
+}
+
 cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y) {
     const float sx = (float)(1.0 / sqrt((double)c->nx)), sy = (float)(1.0 / sqrt((double)c->ny));
     const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->ny * TXG + c->ny + c->nx) * sizeof(float2);
+    prof_begin(c, KID_INIT_GEN);
+    k_trunc_flags<<<4 * 152, 256, 0, c->stream>>>(d_y, (int64_t)c->nc * c->total, c->d_scal, c->d_tflag);
+    prof_end(c, KID_INIT_GEN);
     dim3 grid(c->nx / TXG, c->q);
     DISPATCH_P(c->py, {
         prof_begin(c, KID_INIT_GEN);
         k_init_gen<P_><<<grid, 256, smem, c->stream>>>(d_y, c->d_idx, c->d_framerows, c->d_lineptr, c->d_rowoff,
                                                        c->d_rowcnt, c->d_fpk, c->d_mks, c->d_smaps, c->d_scal,
-                                                       c->d_Z, c->d_X0, c->nx, c->q, c->nc, c->d_twy, c->d_twx, sy,
-                                                       sx);
+                                                       c->d_tflag, c->d_Z, c->d_X0, c->nx, c->q, c->nc, c->d_twy,
+                                                       c->d_twx, sy, sx, (float)(1.0 / (double)c->nx));
         prof_end(c, KID_INIT_GEN);
     });
     return cudaGetLastError();
