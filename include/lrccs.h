@@ -63,13 +63,18 @@ typedef enum lrccs_status {
     LRCCS_E_UNSUPPORTED = 8       /* valid input outside this build's scope (see above) */
 } lrccs_status;
 
-/* Arithmetic of the transforms.  This build has the FP32 FFT path only; the
- * tensor-core DFT-as-GEMM forms are reserved values that lrccs_create refuses
- * with LRCCS_E_UNSUPPORTED. */
+/* Arithmetic of the iteration's forward transform (the DFT along ky of the
+ * coil images of U on the sampled rows).  The precision forms run it as a
+ * dense GEMM with the DFT matrix of the sampled rows on the tcgen05 tensor
+ * cores, accumulating in FP32 (Sec. II-A's A_k U, F as a matrix):
+ *   BF16X3: operands split into bf16 hi + lo, three products (hi hi, hi lo, lo hi);
+ *   FP16S : one FP16 product, the U-side tile scaled per CTA by a power of two.
+ * Everything else (the adjoint, the Grams, the solves, the QR, the init) is
+ * the same in every form.  Other values: LRCCS_E_UNSUPPORTED. */
 typedef enum lrccs_precision {
     LRCCS_PREC_FP32_FFT = 0,      /* FP32 fast Fourier transforms, FP32 accumulation */
-    LRCCS_PREC_BF16X3_GEMM = 1,   /* (not built) DFT as GEMM, 3-term BF16 split */
-    LRCCS_PREC_FP16S_GEMM = 2     /* (not built) DFT as GEMM, FP16 with per-tile scaling */
+    LRCCS_PREC_BF16X3_GEMM = 1,   /* DFT as a tcgen05 GEMM, 3-term BF16 split products */
+    LRCCS_PREC_FP16S_GEMM = 2     /* DFT as a tcgen05 GEMM, FP16 with per-tile scaling */
 } lrccs_precision;
 
 typedef struct lrccs_dims {
@@ -416,6 +421,14 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
 #define LRCCS_NOALLOC_MAX_ENTRIES ((int64_t)268435456)
 lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor, double *d_gamma,
                                            void *cuda_stream);
+
+/* Diagnostics: the iteration's forward transform of the current subspace,
+ * T_j = F_y (d_j o U) on the k-space rows some frame samples (FP32 FFT, or the
+ * tensor-core DFT GEMM of the context's precision form), copied to d_T as
+ * complex64 [j][ky][x][l] (C x ny x nx x r; rows no frame samples are not
+ * written).  bytes must be at least C n r 8.  Synchronises.  Errors:
+ * LRCCS_E_INVALID, LRCCS_E_STATE (no lrccs_init yet), LRCCS_E_CUDA. */
+lrccs_status lrccs_forward_transform(lrccs_ctx *ctx, void *d_T, size_t bytes);
 
 /* Phase timing of the GD/QR kernel (measurement support, like the paper's
  * per-step timing markers, Sec. V).  enable != 0 allocates a stamp buffer and

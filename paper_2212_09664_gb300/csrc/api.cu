@@ -33,6 +33,7 @@ cudaError_t configure_kernels_init(int max_smem);
 cudaError_t configure_kernels_iter(int max_smem);
 cudaError_t configure_kernels_gd(int max_smem);
 cudaError_t configure_kernels_general(int max_smem);
+cudaError_t configure_kernels_tc(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -120,8 +121,9 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
                 "ncoil in [1,64]; 0 <= rank <= rank_max <= 16)");
         return LRCCS_E_INVALID;
     }
-    if (d.precision != LRCCS_PREC_FP32_FFT) {
-        set_err(nullptr, "lrccs_create: precision %d is not built (only LRCCS_PREC_FP32_FFT)", d.precision);
+    if (d.precision != LRCCS_PREC_FP32_FFT && d.precision != LRCCS_PREC_BF16X3_GEMM &&
+        d.precision != LRCCS_PREC_FP16S_GEMM) {
+        set_err(nullptr, "lrccs_create: unknown precision %d", d.precision);
         return LRCCS_E_UNSUPPORTED;
     }
     lrccs_ctx *c = new (std::nothrow) lrccs_ctx();
@@ -181,6 +183,8 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
         {(void **)&c->d_framek, (size_t)q * ny * I4}, {(void **)&c->d_mks, (size_t)q * I4},
         {(void **)&c->d_fpk, ((size_t)q + 1) * I4}, {(void **)&c->d_rowoff, (size_t)q * ny * I4},
         {(void **)&c->d_maskc, (size_t)q * n}, {(void **)&c->d_twq, (size_t)q * F2},
+        {(void **)&c->d_tcA0, d.precision != LRCCS_PREC_FP32_FFT ? tc_a_elems(ny) * 2 : 0},
+        {(void **)&c->d_tcA1, d.precision == LRCCS_PREC_BF16X3_GEMM ? tc_a_elems(ny) * 2 : 0},
     };
     size_t need = 0;
     for (const auto &it : plan) need += (it.bytes + 255) & ~(size_t)255;
@@ -232,6 +236,7 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
     if (e == cudaSuccess) e = configure_kernels_iter(optin);
     if (e == cudaSuccess) e = configure_kernels_gd(optin);
     if (e == cudaSuccess) e = configure_kernels_general(optin);
+    if (e == cudaSuccess) e = configure_kernels_tc(optin);
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
@@ -383,6 +388,7 @@ static lrccs_status load_data(lrccs_ctx *c, const void *d_y, const int64_t *d_fr
     } else {
         CK(launch_fill_lines(c));
     }
+    if (c->dims.precision != LRCCS_PREC_FP32_FFT) CK(launch_dft_a(c));   // DFT rows of the sampled rows
     // line masks' init row pass: full rows (nx) for every (frame row, coil), plain
     // and truncated (the general masks' init needs no such buffer)
     const size_t need = c->general ? 0 : (size_t)2 * c->nc * c->n_lines * c->nx;
@@ -1240,7 +1246,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -1331,6 +1337,22 @@ extern "C" lrccs_status lrccs_profile_reset(lrccs_ctx *c) {
         c->prof_ms[k] = 0.0;
     }
     return s;
+}
+
+extern "C" lrccs_status lrccs_forward_transform(lrccs_ctx *c, void *d_T, size_t bytes) {
+    if (!c || !d_T) return LRCCS_E_INVALID;
+    if (!c->initialized || c->need_h) {
+        set_err(c, "lrccs_forward_transform: no data and subspace loaded (lrccs_init first)");
+        return LRCCS_E_STATE;
+    }
+    const size_t need = (size_t)c->nc * c->n * c->r * sizeof(float2);
+    if (bytes < need) {
+        set_err(c, "lrccs_forward_transform: destination holds %zu bytes, %zu needed", bytes, need);
+        return LRCCS_E_INVALID;
+    }
+    CK(launch_forward(c));
+    CK(cudaMemcpyAsync(d_T, c->d_T, need, cudaMemcpyDeviceToDevice, c->stream));
+    return sync_status(c);
 }
 
 extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *out) {

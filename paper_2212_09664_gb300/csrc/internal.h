@@ -47,7 +47,9 @@ enum {
     KID_UNION, KID_FILL_GEN, KID_INIT_GEN, KID_FWD_ROWS, KID_SAMPLE_GRAM, KID_SOLVE_GEN, KID_SAMPLE_W,
     KID_ADJ_ROWS, KID_MEAN_RESID_GEN,
     // model-error correction (Alg. 3) and online tracking (Alg. 5)
-    KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT, KID_COUNT
+    KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT,
+    // precision forms of the forward transform (tcgen05 GEMM)
+    KID_TC_A, KID_TC_GEMM, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -174,6 +176,9 @@ struct lrccs_ctx {
     float2 *d_mec;               // 5 vectors of mec_nch * n * mec_w: E, S, P, W, and M_prev (MEC-2)
     double *d_mscal;             // gamma, alpha, beta (q each), then reduction partials
     double *d_mout;              // 8 FP64 results of the MEC-2 reductions
+    // precision forms: the DFT matrix of the sampled rows as tensor-core
+    // operand tiles (bf16 hi / lo, or fp16 in d_tcA0)
+    uint16_t *d_tcA0, *d_tcA1;
     float2 *d_twq;               // q twiddles exp(-2 pi i t / q) of the temporal DFT
     int mec_w, mec_nch;
 };
@@ -212,6 +217,11 @@ cudaError_t launch_tdft_inv(lrccs_ctx *c, const float2 *M, float omega, float2 *
 size_t mec_scal_count(int n, int q, int w);
 size_t frame_gram_part_count(int q, int rmax);   // doubles of d_fpart
 cudaError_t launch_bstep(lrccs_ctx *c);   // B-step only (forward transforms, Grams, solve) at the current U
+// precision forms (kernels_tc.cu)
+cudaError_t launch_dft_a(lrccs_ctx *c);
+cudaError_t launch_forward(lrccs_ctx *c);   // the iteration's forward transform of U (FFT or GEMM)
+cudaError_t launch_fwd_gemm(lrccs_ctx *c);
+size_t tc_a_elems(int ny);
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);

@@ -450,7 +450,11 @@ cudaError_t launch_adj_cols_to(lrccs_ctx *c, float2 *dst, int r) {
     return el;
 }
 
-static cudaError_t launch_fwd_cols(lrccs_ctx *c) { return launch_fwd_cols_on(c, c->d_U, c->r); }
+static cudaError_t launch_fwd_cols(lrccs_ctx *c) {
+    // the precision forms run the sampled rows' DFT as a tensor-core GEMM
+    if (c->dims.precision != LRCCS_PREC_FP32_FFT) return launch_fwd_gemm(c);
+    return launch_fwd_cols_on(c, c->d_U, c->r);
+}
 // the iteration's coil-summed inverse transform goes to the U+ buffer (free during iterations)
 static cudaError_t launch_adj_cols(lrccs_ctx *c) { return launch_adj_cols_to(c, c->d_Up, c->r); }
 
@@ -475,6 +479,15 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
     if (e != cudaSuccess) return e;
     // F: gradient, GD step and CholeskyQR2 (one cooperative launch)
     return launch_gdqr(c, 1);
+}
+
+// The iteration's forward transform alone (FP32 FFT or, for the precision
+// forms, the tensor-core GEMM): d_T <- F_y(d_j o U) on the sampled rows.
+cudaError_t launch_forward(lrccs_ctx *c) {
+    if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    cudaError_t el = launch_fwd_cols(c);
+    if (el != cudaSuccess) return el;
+    return cudaGetLastError();
 }
 
 // The B-step alone at the current U (U^H Z already in the totals): forward

@@ -74,6 +74,7 @@ _sig = {
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
     "lrccs_gdqr_phases": (_st, [_vp, C.c_int32, C.POINTER(C.c_double)]),
+    "lrccs_forward_transform": (_st, [_vp, _vp, C.c_size_t]),
     "lrccs_context_bytes": (_st, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lrccs_track_minibatch_async": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.c_void_p]),
     "lrccs_ticket_query": (_st, [_vp, C.c_void_p, C.POINTER(C.c_int32)]),
@@ -268,6 +269,10 @@ def lrccs_set_state(ctx, state: bytes):
     _check(ctx, _lib.lrccs_set_state(ctx, state, len(state)))
 
 
+def lrccs_forward_transform(ctx, T):
+    _check(ctx, _lib.lrccs_forward_transform(ctx, _ptr(T), T.numel() * T.element_size()))
+
+
 def lrccs_gdqr_phases(ctx, enable: bool = True, read: bool = False):
     """Phase timing of the GD/QR kernel: returns [(mean, max) cycles] per interval when read."""
     out = (C.c_double * 22)() if read else None
@@ -306,14 +311,15 @@ class Solver:
     All tensors live on the current CUDA device; outputs are new torch tensors.
     """
 
-    def __init__(self, ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None):
+    def __init__(self, ny, nx, q, ncoil, rank, rank_max=0, params: Params = None, stream=None,
+                 precision=PREC_FP32_FFT):
         import torch
 
         self._torch = torch
         self.ny, self.nx, self.q, self.nc = ny, nx, q, ncoil
         self.n = ny * nx
         self.stream = stream
-        self.ctx = lrccs_create(ny, nx, q, ncoil, rank, rank_max, params, stream)
+        self.ctx = lrccs_create(ny, nx, q, ncoil, rank, rank_max, params, stream, precision)
         self.r = rank
 
     def close(self):
