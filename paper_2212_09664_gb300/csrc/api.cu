@@ -84,7 +84,7 @@ static void free_all(lrccs_ctx *c) {
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
                     c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart,
-                    c->d_tflag};
+                    c->d_tflag, c->d_tcA0, c->d_tcA1, c->d_tcscale};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -185,6 +185,7 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
         {(void **)&c->d_maskc, (size_t)q * n}, {(void **)&c->d_twq, (size_t)q * F2},
         {(void **)&c->d_tcA0, d.precision != LRCCS_PREC_FP32_FFT ? tc_a_elems(ny) * 2 : 0},
         {(void **)&c->d_tcA1, d.precision == LRCCS_PREC_BF16X3_GEMM ? tc_a_elems(ny) * 2 : 0},
+        {(void **)&c->d_tcscale, (1 + ((size_t)c->nx * rmax + 127) / 128) * sizeof(float)},
     };
     size_t need = 0;
     for (const auto &it : plan) need += (it.bytes + 255) & ~(size_t)255;

@@ -179,6 +179,7 @@ struct lrccs_ctx {
     // precision forms: the DFT matrix of the sampled rows as tensor-core
     // operand tiles (bf16 hi / lo, or fp16 in d_tcA0)
     uint16_t *d_tcA0, *d_tcA1;
+    float *d_tcscale;            // FP16S: [0] max over the coil maps, then one scale per N tile
     float2 *d_twq;               // q twiddles exp(-2 pi i t / q) of the temporal DFT
     int mec_w, mec_nch;
 };

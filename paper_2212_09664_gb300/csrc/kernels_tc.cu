@@ -126,6 +126,48 @@ __global__ void k_dft_a(const int32_t *__restrict__ usedrows, int n_used, int ny
     }
 }
 
+// ---------------------------------------------------------------- FP16S scales
+
+// Per N tile (128 columns (x, l) of U): the power of two that puts the tile's
+// largest possible coil product near 2^14 (FP16 holds up to 65504):
+// max |d_j o U| <= max |d| max_tile |U|, with max |d| over every coil and pixel
+// taken at data load (dmax).
+__global__ void __launch_bounds__(TC_N) k_tile_scale(const float2 *__restrict__ U, int ny, int N, const float *dmax,
+                                                     float *__restrict__ tscale) {
+    __shared__ float s_m[TC_N / 32];
+    const int ng = blockIdx.x * TC_N + threadIdx.x;
+    float mx = 0.f;
+    if (ng < N)
+        for (int y = 0; y < ny; ++y) {
+            const float2 u = U[(size_t)y * N + ng];
+            mx = fmaxf(mx, fmaxf(fabsf(u.x), fabsf(u.y)));
+        }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < TC_N / 32; ++w) m = fmaxf(m, s_m[w]);
+        m *= *dmax;
+        tscale[blockIdx.x] = m > 0.f ? ldexpf(1.f, 14 - (int)ceilf(log2f(m))) : 1.f;
+    }
+}
+
+// dmax = max |Re|, |Im| over the coil maps (once per data load)
+__global__ void k_map_max(const float2 *__restrict__ smaps, size_t count, float *dmax) {
+    __shared__ float s_m[8];
+    float mx = 0.f;
+    for (size_t e = threadIdx.x; e < count; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(smaps[e].x), fabsf(smaps[e].y)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_m[w]);
+        *dmax = 2.f * m;   // |d| <= |Re| + |Im| <= 2 max(|Re|, |Im|)
+    }
+}
+
 // ---------------------------------------------------------------- the GEMM
 
 template <int MODE>   // 1 = BF16X3, 2 = FP16S
@@ -133,49 +175,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
                                                          const float2 *__restrict__ smaps,
                                                          const uint16_t *__restrict__ A0,
                                                          const uint16_t *__restrict__ A1,
-                                                         const int32_t *__restrict__ usedrows, float2 *__restrict__ T,
+                                                         const int32_t *__restrict__ usedrows,
+                                                         const float *__restrict__ tscale, float2 *__restrict__ T,
                                                          int ny, int nx, int r, int n_used, unsigned int *status) {
     constexpr int NT = MODE == 1 ? 4 : 2;   // operand tiles: A_hi, A_lo, B_hi, B_lo | A, B
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    uint8_t *sA0 = tc_smem, *sA1 = tc_smem + TC_TILE * 2;
-    uint8_t *sB0 = tc_smem + (NT / 2) * TC_TILE * 2, *sB1 = sB0 + TC_TILE * 2;
-    __shared__ __align__(8) uint64_t mbar;
+    // two stages of NT tiles: chunk kc is produced into stage kc & 1 while the
+    // MMAs of chunk kc - 1 read the other stage
+    constexpr int STAGE = NT * TC_TILE * 2;   // bytes per stage
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ float s_max[TC_THREADS / 32];
     const int t = threadIdx.x;
     const int bm = blockIdx.x, n0 = blockIdx.y * TC_N, j = blockIdx.z;
     const int N = nx * r, K2 = 2 * ny, KC = K2 / TC_KC;
     const size_t n = (size_t)ny * nx;
-    // this thread's column of B: n = t % 128, and half of each chunk's y values
-    const int bn = t & (TC_N - 1), yh = t >> 7;
+    // this thread's column of B: n = t % 128, and core-matrix columns kb =
+    // t / 128, t / 128 + 2, ... of each chunk (4 y values, 8 k, one 16-byte row each)
+    const int bn = t & (TC_N - 1), kb0 = t >> 7;
     const int ng = n0 + bn;
     const bool col_ok = ng < N;
     const int x = col_ok ? ng / r : 0;
-    const float2 *Ucol = U + ng;                          // U[y nx r + ng]
+    const float2 *Ucol = U + (col_ok ? ng : 0);           // U[y nx r + ng]
     const float2 *Scol = smaps + (size_t)j * n + x;       // d_j[y nx + x]
-    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-    // FP16S: the power-of-two scale of this CTA's B tile
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    const uint32_t mb1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
+    // FP16S: the power-of-two scale of this N tile's B (k_tile_scale)
     float bscale = 1.f, binv = 1.f;
     if (MODE == 2) {
-        float mx = 0.f;
-        if (col_ok)
-            for (int y = yh; y < ny; y += 2) {
-                const float2 p = cmul(Scol[(size_t)y * nx], Ucol[(size_t)y * nx * r]);
-                mx = fmaxf(mx, fmaxf(fabsf(p.x), fabsf(p.y)));
-            }
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((t & 31) == 0) s_max[t >> 5] = mx;
-        __syncthreads();
-        mx = 0.f;
-        for (int w = 0; w < TC_THREADS / 32; ++w) mx = fmaxf(mx, s_max[w]);
-        if (mx > 0.f) {
-            const int e = 14 - (int)ceilf(log2f(mx));   // largest entry near 2^14 (FP16 max 65504)
-            bscale = ldexpf(1.f, e);
-            binv = ldexpf(1.f, -e);
-        }
+        bscale = tscale[blockIdx.y];
+        binv = 1.f / bscale;
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb1));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (t < 32) {
@@ -189,8 +221,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
     const uint32_t tmem = tmem_slot;
     bool ok = true;
     for (int kc = 0; kc < KC; ++kc) {
-        if (kc > 0 && !tc_wait(mb, (uint32_t)((kc - 1) & 1))) ok = false;   // the MMAs of chunk kc - 1 read the tiles
+        // stage kc & 1 was last read by the MMAs of chunk kc - 2 (its use kc / 2 - 1)
+        const int st = kc & 1;
+        const uint32_t mbs = st ? mb1 : mb0;
+        if (kc >= 2 && !tc_wait(mbs, (uint32_t)(((kc >> 1) - 1) & 1))) ok = false;
         if (!__syncthreads_and(ok)) break;
+        uint8_t *sA0 = tc_smem + st * STAGE, *sA1 = sA0 + TC_TILE * 2;
+        uint8_t *sB0 = sA0 + (NT / 2) * TC_TILE * 2, *sB1 = sB0 + TC_TILE * 2;
         // A tiles: contiguous 16 KB copies
         {
             const uint4 *g0 = (const uint4 *)(A0 + ((size_t)bm * KC + kc) * TC_TILE);
@@ -200,23 +237,30 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
                 for (int e = t; e < TC_TILE * 2 / 16; e += TC_THREADS) ((uint4 *)sA1)[e] = g1[e];
             }
         }
-        // B tile rows (k = 2 y + c): the coil product of this thread's column for
-        // its 16 y values of the chunk, split / converted
-        for (int i = 0; i < TC_KC / 4; ++i) {
-            const int yl = yh + 2 * i, y = kc * (TC_KC / 2) + yl;
-            float2 p = make_float2(0.f, 0.f);
-            if (col_ok) p = cmul(Scol[(size_t)y * nx], Ucol[(size_t)y * nx * r]);
-            const uint32_t o0 = tc_off(bn, 2 * yl), o1 = tc_off(bn, 2 * yl + 1);
-            if (MODE == 1) {
-                const __nv_bfloat16 hr = __float2bfloat16(p.x), hi = __float2bfloat16(p.y);
-                *(__nv_bfloat16 *)(sB0 + o0) = hr;
-                *(__nv_bfloat16 *)(sB0 + o1) = hi;
-                *(__nv_bfloat16 *)(sB1 + o0) = __float2bfloat16(p.x - __bfloat162float(hr));
-                *(__nv_bfloat16 *)(sB1 + o1) = __float2bfloat16(p.y - __bfloat162float(hi));
-            } else {
-                *(__half *)(sB0 + o0) = __float2half(p.x * bscale);
-                *(__half *)(sB0 + o1) = __float2half(p.y * bscale);
+        // B tile: for each of this thread's core-matrix columns kb, the coil
+        // products of its column for 4 consecutive y (8 k: re, im), split or
+        // scaled and converted, stored as one 16-byte row of the core matrix
+        for (int kb = kb0; kb < TC_KC / 8; kb += TC_THREADS / TC_N) {
+            const int y0 = kc * (TC_KC / 2) + 4 * kb;
+            uint32_t w0[4], w1[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float2 p = make_float2(0.f, 0.f);
+                if (col_ok) p = cmul(__ldg(Scol + (size_t)(y0 + i) * nx), __ldg(Ucol + (size_t)(y0 + i) * nx * r));
+                if (MODE == 1) {
+                    const __nv_bfloat16 hr = __float2bfloat16(p.x), hi = __float2bfloat16(p.y);
+                    const __nv_bfloat16 lr = __float2bfloat16(p.x - __bfloat162float(hr));
+                    const __nv_bfloat16 li = __float2bfloat16(p.y - __bfloat162float(hi));
+                    w0[i] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+                    w1[i] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+                } else {
+                    w0[i] = (uint32_t)__half_as_ushort(__float2half(p.x * bscale)) |
+                            ((uint32_t)__half_as_ushort(__float2half(p.y * bscale)) << 16);
+                }
             }
+            const uint32_t o = tc_off(bn, 8 * kb);
+            *(uint4 *)(sB0 + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            if (MODE == 1) *(uint4 *)(sB1 + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -234,10 +278,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
                     tc_mma(tmem, tc_desc(a1 + ko), tc_desc(b0 + ko), idesc, 1u);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbs));
         }
     }
-    if (ok && !tc_wait(mb, (uint32_t)((KC - 1) & 1))) ok = false;
+    // the last commit covers every earlier MMA of this thread
+    if (ok && !tc_wait(((KC - 1) & 1) ? mb1 : mb0, (uint32_t)(((KC - 1) >> 1) & 1))) ok = false;
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
@@ -291,6 +336,11 @@ cudaError_t launch_dft_a(lrccs_ctx *c) {
     k_dft_a<<<4 * 152, 256, 0, c->stream>>>(c->d_usedrows, c->n_used, c->ny, tc_mtiles(c->n_used), mode, c->d_tcA0,
                                             c->d_tcA1);
     prof_end(c, KID_TC_A);
+    if (mode == 2) {
+        prof_begin(c, KID_TC_A);
+        k_map_max<<<1, 256, 0, c->stream>>>(c->d_smaps, (size_t)c->nc * c->n, c->d_tcscale);
+        prof_end(c, KID_TC_A);
+    }
     return cudaGetLastError();
 }
 
@@ -298,17 +348,23 @@ cudaError_t launch_fwd_gemm(lrccs_ctx *c) {
     const int N = c->nx * c->r;
     dim3 grid(tc_mtiles(c->n_used), (N + TC_N - 1) / TC_N, c->nc);
     cudaError_t e;
+    if (c->dims.precision == LRCCS_PREC_FP16S_GEMM) {
+        prof_begin(c, KID_TC_GEMM);
+        k_tile_scale<<<(N + TC_N - 1) / TC_N, TC_N, 0, c->stream>>>(c->d_U, c->ny, N, c->d_tcscale,
+                                                                    c->d_tcscale + 1);
+        prof_end(c, KID_TC_GEMM);
+    }
     prof_begin(c, KID_TC_GEMM);
     if (c->dims.precision == LRCCS_PREC_BF16X3_GEMM)
-        k_fwd_gemm<1><<<grid, TC_THREADS, 4 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
-                                                                         c->d_usedrows, c->d_T, c->ny, c->nx, c->r,
-                                                                         c->n_used, c->d_status);
+        k_fwd_gemm<1><<<grid, TC_THREADS, 8 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
+                                                                         c->d_usedrows, c->d_tcscale + 1, c->d_T, c->ny, c->nx,
+                                                                         c->r, c->n_used, c->d_status);
     else
-        // the same 64 KB request as BF16X3 (2 tiles used): at most 3 CTAs per SM,
-        // so their 128-column tensor-memory allocations always fit in 512
+        // two stages of 2 tiles (64 KB): at most 3 CTAs per SM, so their
+        // 128-column tensor-memory allocations always fit in 512
         k_fwd_gemm<2><<<grid, TC_THREADS, 4 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
-                                                                         c->d_usedrows, c->d_T, c->ny, c->nx, c->r,
-                                                                         c->n_used, c->d_status);
+                                                                         c->d_usedrows, c->d_tcscale + 1, c->d_T, c->ny, c->nx,
+                                                                         c->r, c->n_used, c->d_status);
     prof_end(c, KID_TC_GEMM);
     e = cudaGetLastError();
     return e;
