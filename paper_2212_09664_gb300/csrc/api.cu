@@ -1247,7 +1247,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

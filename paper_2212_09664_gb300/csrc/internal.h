@@ -49,7 +49,7 @@ enum {
     // model-error correction (Alg. 3) and online tracking (Alg. 5)
     KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT,
     // precision forms of the forward transform (tcgen05 GEMM)
-    KID_TC_A, KID_TC_GEMM, KID_COUNT
+    KID_TC_A, KID_TC_GEMM, KID_TC_SCALE, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 

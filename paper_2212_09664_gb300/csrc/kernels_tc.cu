@@ -153,24 +153,27 @@ __global__ void __launch_bounds__(TC_N) k_tile_scale(const float2 *__restrict__ 
     }
 }
 
-// dmax = max |Re|, |Im| over the coil maps (once per data load)
+// dmax = 2 max(|Re|, |Im|) >= max |d| over the coil maps (once per data load;
+// *dmax zeroed first).  Non-negative floats order like their bit patterns, so
+// the blocks combine with an integer atomicMax.
 __global__ void k_map_max(const float2 *__restrict__ smaps, size_t count, float *dmax) {
     __shared__ float s_m[8];
     float mx = 0.f;
-    for (size_t e = threadIdx.x; e < count; e += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(smaps[e].x), fabsf(smaps[e].y)));
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fmaxf(fabsf(smaps[e].x), fabsf(smaps[e].y)));
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         float m = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_m[w]);
-        *dmax = 2.f * m;   // |d| <= |Re| + |Im| <= 2 max(|Re|, |Im|)
+        atomicMax((int *)dmax, __float_as_int(2.f * m));   // |d| <= |Re| + |Im|
     }
 }
 
 // ---------------------------------------------------------------- the GEMM
 
-template <int MODE>   // 1 = BF16X3, 2 = FP16S
+template <int MODE, int NSTAGE>   // MODE 1 = BF16X3, 2 = FP16S; NSTAGE shared-memory stages (1 or 2)
 __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restrict__ U,
                                                          const float2 *__restrict__ smaps,
                                                          const uint16_t *__restrict__ A0,
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
                                                          int ny, int nx, int r, int n_used, unsigned int *status) {
     constexpr int NT = MODE == 1 ? 4 : 2;   // operand tiles: A_hi, A_lo, B_hi, B_lo | A, B
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    // two stages of NT tiles: chunk kc is produced into stage kc & 1 while the
-    // MMAs of chunk kc - 1 read the other stage
+    // NSTAGE stages of NT tiles: with two, chunk kc is produced into stage
+    // kc & 1 while the MMAs of chunk kc - 1 read the other stage
     constexpr int STAGE = NT * TC_TILE * 2;   // bytes per stage
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
@@ -221,10 +224,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
     const uint32_t tmem = tmem_slot;
     bool ok = true;
     for (int kc = 0; kc < KC; ++kc) {
-        // stage kc & 1 was last read by the MMAs of chunk kc - 2 (its use kc / 2 - 1)
-        const int st = kc & 1;
+        // the stage was last read by the MMAs of chunk kc - NSTAGE (barrier use
+        // kc / NSTAGE - 1 of that stage's mbarrier)
+        const int st = NSTAGE == 2 ? (kc & 1) : 0;
         const uint32_t mbs = st ? mb1 : mb0;
-        if (kc >= 2 && !tc_wait(mbs, (uint32_t)(((kc >> 1) - 1) & 1))) ok = false;
+        const int use = NSTAGE == 2 ? (kc >> 1) : kc;
+        if (kc >= NSTAGE && !tc_wait(mbs, (uint32_t)((use - 1) & 1))) ok = false;
         if (!__syncthreads_and(ok)) break;
         uint8_t *sA0 = tc_smem + st * STAGE, *sA1 = sA0 + TC_TILE * 2;
         uint8_t *sB0 = sA0 + (NT / 2) * TC_TILE * 2, *sB1 = sB0 + TC_TILE * 2;
@@ -282,7 +287,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_fwd_gemm(const float2 *__restric
         }
     }
     // the last commit covers every earlier MMA of this thread
-    if (ok && !tc_wait(((KC - 1) & 1) ? mb1 : mb0, (uint32_t)(((KC - 1) >> 1) & 1))) ok = false;
+    {
+        const int st = NSTAGE == 2 ? ((KC - 1) & 1) : 0, use = NSTAGE == 2 ? ((KC - 1) >> 1) : (KC - 1);
+        if (ok && !tc_wait(st ? mb1 : mb0, (uint32_t)(use & 1))) ok = false;
+    }
     ok = __syncthreads_and(ok);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
@@ -338,7 +346,8 @@ cudaError_t launch_dft_a(lrccs_ctx *c) {
     prof_end(c, KID_TC_A);
     if (mode == 2) {
         prof_begin(c, KID_TC_A);
-        k_map_max<<<1, 256, 0, c->stream>>>(c->d_smaps, (size_t)c->nc * c->n, c->d_tcscale);
+        cudaMemsetAsync(c->d_tcscale, 0, sizeof(float), c->stream);
+        k_map_max<<<152, 256, 0, c->stream>>>(c->d_smaps, (size_t)c->nc * c->n, c->d_tcscale);
         prof_end(c, KID_TC_A);
     }
     return cudaGetLastError();
@@ -349,20 +358,22 @@ cudaError_t launch_fwd_gemm(lrccs_ctx *c) {
     dim3 grid(tc_mtiles(c->n_used), (N + TC_N - 1) / TC_N, c->nc);
     cudaError_t e;
     if (c->dims.precision == LRCCS_PREC_FP16S_GEMM) {
-        prof_begin(c, KID_TC_GEMM);
+        prof_begin(c, KID_TC_SCALE);
         k_tile_scale<<<(N + TC_N - 1) / TC_N, TC_N, 0, c->stream>>>(c->d_U, c->ny, N, c->d_tcscale,
                                                                     c->d_tcscale + 1);
-        prof_end(c, KID_TC_GEMM);
+        prof_end(c, KID_TC_SCALE);
     }
     prof_begin(c, KID_TC_GEMM);
     if (c->dims.precision == LRCCS_PREC_BF16X3_GEMM)
-        k_fwd_gemm<1><<<grid, TC_THREADS, 8 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
+        // one stage of 4 tiles (64 KB): three CTAs per SM overlap one another's
+        // operand production and MMAs (two stages, 128 KB, measured slower)
+        k_fwd_gemm<1, 1><<<grid, TC_THREADS, 4 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
                                                                          c->d_usedrows, c->d_tcscale + 1, c->d_T, c->ny, c->nx,
                                                                          c->r, c->n_used, c->d_status);
     else
         // two stages of 2 tiles (64 KB): at most 3 CTAs per SM, so their
         // 128-column tensor-memory allocations always fit in 512
-        k_fwd_gemm<2><<<grid, TC_THREADS, 4 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
+        k_fwd_gemm<2, 2><<<grid, TC_THREADS, 4 * TC_TILE * 2, c->stream>>>(c->d_U, c->d_smaps, c->d_tcA0, c->d_tcA1,
                                                                          c->d_usedrows, c->d_tcscale + 1, c->d_T, c->ny, c->nx,
                                                                          c->r, c->n_used, c->d_status);
     prof_end(c, KID_TC_GEMM);
@@ -371,7 +382,7 @@ cudaError_t launch_fwd_gemm(lrccs_ctx *c) {
 }
 
 cudaError_t configure_kernels_tc(int max_smem) {
-    cudaError_t e = allow_smem(k_fwd_gemm<1>, max_smem);
-    if (e == cudaSuccess) e = allow_smem(k_fwd_gemm<2>, max_smem);
+    cudaError_t e = allow_smem(k_fwd_gemm<1, 1>, max_smem);
+    if (e == cudaSuccess) e = allow_smem(k_fwd_gemm<2, 2>, max_smem);
     return e;
 }
