@@ -192,6 +192,7 @@ cudaError_t launch_compact_general(lrccs_ctx *c, const uint8_t *d_mask) {
 // along ky and multiplied by conj(d_j) into the coil sum.  Nothing the size of
 // full k-space rows goes through memory.
 #define TXG 16
+#define IG_STAGE 4096   // samples of one coil staged at a time (a row has at most nx <= 256)
 template <int P>
 __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, const int32_t *__restrict__ idx,
                                                   const int32_t *__restrict__ framerows,
@@ -211,6 +212,10 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
     float2 *s_S = tile + NY * TP;         // NY * TXG
     float2 *s_twy = s_S + NY * TXG;       // NY
     float2 *s_twx = s_twy + NY;           // nx
+    float2 *s_y = s_twx + 256;            // IG_STAGE staged samples of one coil
+    int16_t *s_kx = (int16_t *)(s_y + IG_STAGE);
+    uint8_t *s_tr = (uint8_t *)(s_kx + IG_STAGE);
+    __shared__ int s_grp[3];
     const int k = blockIdx.y, x0 = blockIdx.x * TXG;
     const int n = NY * nx;
     load_twiddles(s_twy, g_twy, NY);
@@ -225,27 +230,54 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
         for (int e = threadIdx.x; e < NY * TP; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
         for (int e = threadIdx.x; e < NY * TXG; e += blockDim.x)
             s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXG) * nx + x0 + (e % TXG)];
-        __syncthreads();
         const int64_t yb = (int64_t)nc * f0 + (int64_t)j * mk;   // sample f0 + s of coil j at y[yb + s]
-        for (int e = threadIdx.x; e < L * TXG; e += blockDim.x) {
-            const int li = e / TXG, xx = e - li * TXG, x = x0 + xx;
-            const int ky = framerows[lp + li];
-            const int off = rowoff[k * NY + ky], cnt = rowcnt[k * NY + ky];
-            float2 vp = make_float2(0.f, 0.f), vt = make_float2(0.f, 0.f);
-            for (int s = off; s < off + cnt; ++s) {
-                const float2 a = __ldg(y + yb + (s - f0));
-                const int kx = __ldg(idx + s) - ky * nx;
-                // (kx x) mod nx without an integer division: kx x < 2^16 is exact in FP32
-                const int p = kx * x;
-                int m = p - nx * (int)((float)p * inv_nx);
-                m += m < 0 ? nx : 0;
-                m -= m >= nx ? nx : 0;
-                const float2 w = cconj(s_twx[m]);   // e^{+2 pi i kx x / nx}
-                cfma(vp, a, w);
-                if (!tflag[yb + (s - f0)]) cfma(vt, a, w);   // kept by the truncation (|y|^2 <= gamma)
+        // the frame's rows in groups whose samples fit the staging area
+        for (int g0 = 0; g0 < L;) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int g1 = g0, tot = 0;
+                while (g1 < L) {
+                    const int c = rowcnt[k * NY + framerows[lp + g1]];
+                    if (g1 > g0 && tot + c > IG_STAGE) break;
+                    tot += c;
+                    ++g1;
+                }
+                s_grp[0] = g1;
+                s_grp[1] = rowoff[k * NY + framerows[lp + g0]];
+                s_grp[2] = tot;
             }
-            tile[ky * TP + 2 * xx] = cscale(vp, sx);
-            tile[ky * TP + 2 * xx + 1] = cscale(vt, sx);
+            __syncthreads();
+            const int g1 = s_grp[0], sbase = s_grp[1], scnt = s_grp[2];
+            // stage the group's samples of coil j: value (zeroed in the truncated
+            // copy when |y|^2 > gamma) and kx
+            for (int e = threadIdx.x; e < scnt; e += blockDim.x) {
+                const int s = sbase + e;
+                const float2 a = __ldg(y + yb + (s - f0));
+                s_y[e] = a;
+                s_kx[e] = (int16_t)(__ldg(idx + s) % nx);
+                s_tr[e] = tflag[yb + (s - f0)];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < (g1 - g0) * TXG; e += blockDim.x) {
+                const int li = g0 + e / TXG, xx = e % TXG, x = x0 + xx;
+                const int ky = framerows[lp + li];
+                const int off = rowoff[k * NY + ky] - sbase, cnt = rowcnt[k * NY + ky];
+                float2 vp = make_float2(0.f, 0.f), vt = make_float2(0.f, 0.f);
+                for (int s = off; s < off + cnt; ++s) {
+                    const float2 a = s_y[s];
+                    // (kx x) mod nx without an integer division: kx x < 2^16 is exact in FP32
+                    const int p = (int)s_kx[s] * x;
+                    int m = p - nx * (int)((float)p * inv_nx);
+                    m += m < 0 ? nx : 0;
+                    m -= m >= nx ? nx : 0;
+                    const float2 w = cconj(s_twx[m]);   // e^{+2 pi i kx x / nx}
+                    cfma(vp, a, w);
+                    if (!s_tr[s]) cfma(vt, a, w);   // kept by the truncation (|y|^2 <= gamma)
+                }
+                tile[ky * TP + 2 * xx] = cscale(vp, sx);
+                tile[ky * TP + 2 * xx + 1] = cscale(vt, sx);
+            }
+            g0 = g1;
         }
         __syncthreads();
         fft::tile_dft<NY, true>(tile, TP, 2 * TXG, s_twy, sy);
@@ -283,7 +315,8 @@ __global__ void k_trunc_flags(const float2 *__restrict__ y, int64_t count, const
 
 cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y) {
     const float sx = (float)(1.0 / sqrt((double)c->nx)), sy = (float)(1.0 / sqrt((double)c->ny));
-    const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->ny * TXG + c->ny + c->nx) * sizeof(float2);
+    const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->ny * TXG + c->ny + 256 + IG_STAGE) * sizeof(float2) +
+                        (size_t)IG_STAGE * (sizeof(int16_t) + 1);
     prof_begin(c, KID_INIT_GEN);
     k_trunc_flags<<<4 * 152, 256, 0, c->stream>>>(d_y, (int64_t)c->nc * c->total, c->d_scal, c->d_tflag);
     prof_end(c, KID_INIT_GEN);
