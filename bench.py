@@ -629,6 +629,107 @@ def radial_leg(dev, stream, steps=5, warmup=3):
                        "the oracle's 50-iteration solve at this size takes too long for the bench")
 
 
+BATCH_SLICES = 32
+
+
+def batch_specs(seed=0x5EED0004):
+    """The batched form's 32 slices, drawn from the seed: image side from
+    {128, 160, 192, 224, 256}, 24-96 frames, 8-32 coils, rank 6-14, 1D
+    variable-density lines (even slices) or golden-angle pseudo-radial spokes
+    (odd slices) at 4x-12x acceleration.  Exactly low-rank spectra plus 1%
+    noise (cheap to generate; the solver's cost depends only on the shapes)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(BATCH_SLICES):
+        side = int(rng.choice([128, 160, 192, 224, 256]))
+        q = int(rng.integers(24, 97))
+        r = int(rng.integers(6, 15))
+        sp = dict(kind="lowrank", ny=side, nx=side, q=q, nc=int(rng.integers(8, 33)), rank=r, noise=0.01)
+        accel = float(rng.uniform(4.0, 12.0))
+        if i % 2 == 0:
+            sp.update(mask_kind="lines_vd", accel=accel)
+        else:
+            sp.update(mask_kind="radial", spokes=max(4, int(round(side / accel))))
+        out.append(sp)
+    return out
+
+
+def batched_leg(dev, steps=3):
+    """The batched form: 32 independent slices of uneven sizes, each loaded by
+    its own lrccs_init and given a launch plan by the autotuner (lrccs_autotune,
+    plans cached in a file), then 50 iterations of all of them as ONE graph
+    launch (lrccs_batch_iterate), timed with CUDA events; beside it the same
+    slices iterated one context at a time (one graph launch per slice)."""
+    import tempfile
+
+    import torch
+
+    from paper_2212_09664_gb300 import lrccs, synth
+
+    specs = batch_specs()
+    stream = torch.cuda.Stream(device=dev)
+    slices, tuned = [], []
+    cache = os.path.join(tempfile.gettempdir(), "lrccs_plans_%d.txt" % os.getpid())
+    t0 = time.perf_counter()
+    for i, sp in enumerate(specs):
+        p = synth.make_problem(sp, seed=0x5EED0200 + i)
+        s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+        inp = tuple(torch.from_numpy(a).to(dev) for a in (p.y, p.frame_ptr, p.mask, p.smaps))
+        s.init(*inp)
+        pl = lrccs.lrccs_autotune(s.ctx, 3, cache)
+        tuned.append((pl.fwd_tx, pl.coil_groups, pl.row_groups))
+        slices.append((p, s, inp))
+    t_setup = time.perf_counter() - t0
+    batch = lrccs.lrccs_batch_create([s.ctx for _, s, _ in slices], stream)
+    fi = sum(p.q for p, _, _ in slices) * T_ITER
+
+    def reinit():
+        for _, s, inp in slices:
+            s.init(*inp)
+
+    reinit()
+    lrccs.lrccs_batch_iterate(batch, T_ITER)       # captures every slice's graph, builds the batch graph
+    torch.cuda.synchronize()
+    one = []
+    for _ in range(steps):
+        reinit()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        lrccs.lrccs_batch_iterate(batch, T_ITER)
+        b.record(stream)
+        torch.cuda.synchronize()
+        one.append(a.elapsed_time(b))
+    sep = []
+    for _ in range(steps):
+        reinit()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _, s, _ in slices:
+            s.iterate(T_ITER)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sep.append(a.elapsed_time(b))
+    lrccs.lrccs_batch_destroy(batch)
+    for _, s, _ in slices:
+        s.close()
+    ms1, ms2 = min(one), min(sep)
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
+    return dict(slices=len(slices), frame_iterations_per_batch=fi, value=fi / (ms1 / 1e3), unit=UNIT,
+                ms_per_batch=ms1, one_launch_per_slice=dict(value=fi / (ms2 / 1e3), ms=ms2),
+                setup_s=t_setup, plans_tuned=tuned,
+                shapes=[dict(side=sp["ny"], q=sp["q"], coils=sp["nc"], rank=sp["rank"], masks=sp["mask_kind"])
+                        for sp in specs],
+                note="iterations only (each slice's lrccs_init runs before the timed launch); the slices run one "
+                     "after another inside the graph, since the GD/QR kernel of each is a cooperative launch")
+
+
 def alg1_leg(p, dev, stream, reps=5):
     """Full Alg. 1 on the workload through the C ABI: the mean step
     (lrccs_mean_step, CGLS tol 1e-3, <= 10 iterations, then y~), Alg. 2 on y~
@@ -705,6 +806,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the mini-batch tracking latency leg")
     ap.add_argument("--no-comparators", action="store_true", help="skip the cuFFT / cuBLAS comparator timings")
     ap.add_argument("--no-radial", action="store_true", help="skip the 256 x 256 pseudo-radial workload leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-slice batched-form leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -874,6 +976,11 @@ def main():
             line["radial_fp32"] = radial_leg(dev, stream)
         except Exception as e:
             line["radial_fp32"] = dict(error="%s: %s" % (type(e).__name__, e))
+    if ws == 1 and not args.no_batch:
+        try:
+            line["batched"] = batched_leg(dev)
+        except Exception as e:
+            line["batched"] = dict(error="%s: %s" % (type(e).__name__, e))
     sv_check = None
     if ws == 1 and not args.no_serving:
         try:

@@ -104,6 +104,18 @@ typedef struct lrccs_params {
     double eta_decay;      /* 1    :   k = iterations since eta was set (larger steps first) */
 } lrccs_params;
 
+/* Launch plan of the transform kernels (tile and grouping choices that do not
+ * change the result's definition, only its speed and summation grouping): a
+ * zero field keeps the built-in default.
+ *   fwd_tx      : image columns per block of the forward column transform
+ *                 (even, divides nx, fwd_tx * r <= 256, and fits shared memory)
+ *   coil_groups : coil groups (thread-block cluster size, 1..8) of the column
+ *                 adjoint and the line-mask row passes
+ *   row_groups  : coil groups (1..8) of the general-mask row transforms */
+typedef struct lrccs_plan {
+    int32_t fwd_tx, coil_groups, row_groups, reserved;
+} lrccs_plan;
+
 typedef struct lrccs_iter_info {
     int32_t t;          /* iterations completed since lrccs_init */
     int32_t exited;     /* 1 if the exit test fired */
@@ -421,6 +433,42 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
 #define LRCCS_NOALLOC_MAX_ENTRIES ((int64_t)268435456)
 lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor, double *d_gamma,
                                            void *cuda_stream);
+
+/* Set or read the context's launch plan (the next iterations use it; a
+ * captured iteration graph is rebuilt).  A field that does not fit the
+ * context's shape is ignored (the default is used).  Errors: LRCCS_E_INVALID. */
+lrccs_status lrccs_set_plan(lrccs_ctx *ctx, const lrccs_plan *plan);
+lrccs_status lrccs_get_plan(lrccs_ctx *ctx, lrccs_plan *plan);
+
+/* Autotuner of the launch plan (measurement-driven, per problem shape): after
+ * lrccs_init, times n_iter iterations (directly launched, CUDA events on the
+ * context's stream, best of 2) for every candidate plan -- fwd_tx in {2, 4,
+ * 8, 16, 32}, coil_groups in {1, 2, 3, 4, 6, 8} and, for general masks,
+ * row_groups in {1, 2, 4, 8}, each within the shape's limits, one field at a
+ * time from the defaults -- applies the fastest, and restores the solver
+ * state (U, U_{t-1}, B, step size, right-hand sides), so the solve continues
+ * exactly as if it had not been tuned.  cache_path (NULL: no cache) names a
+ * text file of tuned plans, one line per shape (ny nx q C r mask-kind
+ * precision fwd_tx coil_groups row_groups): a shape found there is applied
+ * without timing; a newly tuned one is appended.  out (may be NULL) receives
+ * the plan.  Synchronises.  Errors: LRCCS_E_STATE (no init), LRCCS_E_CUDA. */
+lrccs_status lrccs_autotune(lrccs_ctx *ctx, int32_t n_iter, const char *cache_path, lrccs_plan *out);
+
+/* ---- Batched form: many independent slices, one graph launch ----------------
+ * A batch holds contexts of independent problems (slices of uneven sizes,
+ * each loaded by its own lrccs_init) and runs n_iter iterations of every one
+ * of them as a single CUDA graph launched on cuda_stream: each context's
+ * captured n_iter-iteration graph becomes a child node, one after another
+ * (the GD/QR kernel of each slice is a cooperative launch that needs the whole
+ * GPU, so the slices are not overlapped).  Every context must use a created
+ * stream (its graph is captured there) and be idle when the batch is
+ * launched; the batch graph is rebuilt when n_iter changes.  Afterwards each
+ * context holds its slice's iterate as after lrccs_iterate.
+ * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (a context without data), LRCCS_E_CUDA. */
+typedef struct lrccs_batch lrccs_batch;
+lrccs_status lrccs_batch_create(lrccs_ctx *const *ctxs, int32_t count, void *cuda_stream, lrccs_batch **out);
+lrccs_status lrccs_batch_iterate(lrccs_batch *batch, int32_t n_iter);
+void lrccs_batch_destroy(lrccs_batch *batch);
 
 /* Diagnostics: the iteration's forward transform of the current subspace,
  * T_j = F_y (d_j o U) on the k-space rows some frame samples (FP32 FFT, or the

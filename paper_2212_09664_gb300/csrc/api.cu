@@ -469,6 +469,8 @@ static void drop_iter_graph(lrccs_ctx *c) {
     cudaStreamSynchronize(c->stream);
     cudaGraphExecDestroy(c->iter_exec);
     c->iter_exec = nullptr;
+    if (c->iter_graph) cudaGraphDestroy(c->iter_graph);
+    c->iter_graph = nullptr;
     for (const prof_rec &r : c->iter_prof) {
         c->event_pool.push_back(r.a);
         c->event_pool.push_back(r.b);
@@ -533,7 +535,12 @@ static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
     }
     c->pending.resize(np0);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->iter_exec, g, 0);
-    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) {
+        c->iter_graph = g;   // kept for batches (child graph nodes)
+        ++c->iter_gen;
+    } else if (g) {
+        cudaGraphDestroy(g);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->iter_exec = nullptr;
@@ -1338,6 +1345,284 @@ extern "C" lrccs_status lrccs_profile_reset(lrccs_ctx *c) {
         c->prof_ms[k] = 0.0;
     }
     return s;
+}
+
+// ---------------------------------------------------------------- launch plan and autotuner
+
+extern "C" lrccs_status lrccs_set_plan(lrccs_ctx *c, const lrccs_plan *plan) {
+    if (!c || !plan) return LRCCS_E_INVALID;
+    c->plan = *plan;
+    drop_iter_graph(c);
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_get_plan(lrccs_ctx *c, lrccs_plan *plan) {
+    if (!c || !plan) return LRCCS_E_INVALID;
+    *plan = c->plan;
+    return LRCCS_OK;
+}
+
+// The solver state one iteration reads and writes: U_t, U_{t-1}, B, the
+// scalars (step size, its schedule counter, SD) and the k_gdqr totals (the
+// right-hand sides U^H Z).
+struct solver_state {
+    std::vector<float2> U, Up, B;
+    std::vector<double> scal;
+    std::vector<double2> tot;
+    int t;
+};
+static lrccs_status save_state(lrccs_ctx *c, solver_state &s, size_t tot_len) {
+    const size_t nu = (size_t)c->n * c->r;
+    s.U.resize(nu);
+    s.Up.resize(nu);
+    s.B.resize((size_t)c->q * c->r);
+    s.scal.resize(SC_COUNT);
+    s.tot.resize(tot_len);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(s.U.data(), c->d_U, nu * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.Up.data(), c->d_Uprev, nu * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.B.data(), c->d_B, s.B.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.scal.data(), c->d_scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s.tot.data(), c->d_tot, tot_len * sizeof(double2), cudaMemcpyDeviceToHost));
+    s.t = c->t;
+    return LRCCS_OK;
+}
+static lrccs_status restore_state(lrccs_ctx *c, const solver_state &s) {
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->d_U, s.U.data(), s.U.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_Uprev, s.Up.data(), s.Up.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_B, s.B.data(), s.B.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_scal, s.scal.data(), SC_COUNT * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_tot, s.tot.data(), s.tot.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+    c->t = s.t;
+    return LRCCS_OK;
+}
+
+// Best of two timed runs of n_iter directly launched iterations under `plan`
+// (ms), from the saved state; < 0 if a launch of the plan failed.
+static double time_plan(lrccs_ctx *c, const lrccs_plan &plan, int n_iter, const solver_state &st) {
+    c->plan = plan;
+    double best = -1.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    for (int rep = 0; rep < 2; ++rep) {
+        if (restore_state(c, st) != LRCCS_OK) break;
+        cudaEventRecord(a, c->stream);
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) e = launch_iteration(c);
+        cudaEventRecord(b, c->stream);
+        if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+            cudaGetLastError();
+            best = -1.0;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best < 0.0 || ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+extern "C" lrccs_status lrccs_autotune(lrccs_ctx *c, int32_t n_iter, const char *cache_path, lrccs_plan *out) {
+    if (!c) return LRCCS_E_INVALID;
+    if (!c->initialized || c->need_h) {
+        set_err(c, "lrccs_autotune: load data first (lrccs_init)");
+        return LRCCS_E_STATE;
+    }
+    if (n_iter < 1) n_iter = 1;
+    if (n_iter > 100) n_iter = 100;
+    char key[160];
+    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d", c->ny, c->nx, c->q, c->nc, c->r, c->general,
+             c->dims.precision);
+    if (cache_path) {   // a tuned plan of this shape: apply it
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[256];
+            bool found = false;
+            while (fgets(line, sizeof(line), f)) {
+                lrccs_plan pl = {};
+                int v[7];
+                if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                           &pl.fwd_tx, &pl.coil_groups, &pl.row_groups) == 10) {
+                    char k2[160];
+                    snprintf(k2, sizeof(k2), "%d %d %d %d %d %d %d", v[0], v[1], v[2], v[3], v[4], v[5], v[6]);
+                    if (!strcmp(k2, key)) {
+                        c->plan = pl;
+                        found = true;
+                    }
+                }
+            }
+            fclose(f);
+            if (found) {
+                drop_iter_graph(c);
+                if (out) *out = c->plan;
+                return LRCCS_OK;
+            }
+        }
+    }
+    const int npm = c->rmax * (c->rmax + 1) / 2;
+    const size_t tot_len = std::max((size_t)2 * npm + (size_t)c->rmax * c->rmax,
+                                    (size_t)c->rmax * c->rmax + (size_t)c->q * c->rmax);
+    solver_state st;
+    lrccs_status s = save_state(c, st, tot_len);
+    if (s != LRCCS_OK) return s;
+    drop_iter_graph(c);
+    lrccs_plan best = {};
+    double best_ms = time_plan(c, best, n_iter, st);
+    if (best_ms < 0.0) {
+        restore_state(c, st);
+        c->plan = lrccs_plan{};
+        set_err(c, "lrccs_autotune: the default plan failed to run");
+        return LRCCS_E_CUDA;
+    }
+    // one field at a time, starting from the defaults
+    const int txs[] = {2, 4, 8, 16, 32}, cgs[] = {1, 2, 3, 4, 6, 8}, rgs[] = {1, 2, 4, 8};
+    for (int v : txs) {
+        if (!fwd_tile_ok(v, c->r, c->nx, c->ny, c->dev_smem_optin)) continue;
+        lrccs_plan p = best;
+        p.fwd_tx = v;
+        const double ms = time_plan(c, p, n_iter, st);
+        if (ms >= 0.0 && ms < best_ms) best_ms = ms, best = p;
+    }
+    for (int v : cgs) {
+        if (v > c->nc) continue;
+        lrccs_plan p = best;
+        p.coil_groups = v;
+        const double ms = time_plan(c, p, n_iter, st);
+        if (ms >= 0.0 && ms < best_ms) best_ms = ms, best = p;
+    }
+    if (c->general)
+        for (int v : rgs) {
+            if (v > c->nc) continue;
+            lrccs_plan p = best;
+            p.row_groups = v;
+            const double ms = time_plan(c, p, n_iter, st);
+            if (ms >= 0.0 && ms < best_ms) best_ms = ms, best = p;
+        }
+    c->plan = best;
+    s = restore_state(c, st);
+    if (s != LRCCS_OK) return s;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %d %d %d\n", key, best.fwd_tx, best.coil_groups, best.row_groups);
+            fclose(f);
+        }
+    }
+    if (out) *out = best;
+    return LRCCS_OK;
+}
+
+// ---------------------------------------------------------------- batched slices
+
+struct lrccs_batch {
+    std::vector<lrccs_ctx *> ctxs;
+    std::vector<unsigned long long> gens;   // each context's graph generation the batch was built from
+    cudaStream_t stream;
+    cudaGraphExec_t exec;
+    int n_iter;
+};
+
+extern "C" lrccs_status lrccs_batch_create(lrccs_ctx *const *ctxs, int32_t count, void *cuda_stream,
+                                           lrccs_batch **out) {
+    if (!ctxs || count < 1 || !out) {
+        set_err(nullptr, "lrccs_batch_create: need contexts and out");
+        return LRCCS_E_INVALID;
+    }
+    *out = nullptr;
+    lrccs_batch *b = new (std::nothrow) lrccs_batch();
+    if (!b) return LRCCS_E_NOMEM;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) {
+            delete b;
+            set_err(nullptr, "lrccs_batch_create: null context");
+            return LRCCS_E_INVALID;
+        }
+        b->ctxs.push_back(ctxs[i]);
+    }
+    b->gens.assign(count, 0);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->exec = nullptr;
+    b->n_iter = 0;
+    *out = b;
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_batch_iterate(lrccs_batch *b, int32_t n_iter) {
+    if (!b || n_iter < 1) {
+        set_err(nullptr, "lrccs_batch_iterate: null batch or n_iter < 1");
+        return LRCCS_E_INVALID;
+    }
+    bool rebuild = !b->exec || b->n_iter != n_iter;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        lrccs_ctx *c = b->ctxs[i];
+        if (!c->initialized) {
+            set_err(nullptr, "lrccs_batch_iterate: context %zu has no data (lrccs_init first)", i);
+            return LRCCS_E_STATE;
+        }
+        if (c->need_h) {
+            lrccs_status s = warm_start(c);
+            if (s != LRCCS_OK) return s;
+        }
+        if (!ensure_iter_graph(c, n_iter)) {
+            set_err(nullptr, "lrccs_batch_iterate: context %zu cannot capture its iterations (created stream needed)",
+                    i);
+            return LRCCS_E_CUDA;
+        }
+        if (b->gens[i] != c->iter_gen) rebuild = true;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return LRCCS_E_CUDA;
+        }
+    }
+    if (rebuild) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        cudaGraph_t parent = nullptr;
+        cudaError_t e = cudaGraphCreate(&parent, 0);
+        cudaGraphNode_t prev = nullptr;
+        for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i) {
+            cudaGraphNode_t node = nullptr;
+            e = cudaGraphAddChildGraphNode(&node, parent, prev ? &prev : nullptr, prev ? 1 : 0,
+                                           b->ctxs[i]->iter_graph);
+            prev = node;
+            b->gens[i] = b->ctxs[i]->iter_gen;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, parent, 0);
+        if (parent) cudaGraphDestroy(parent);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->exec = nullptr;
+            set_err(nullptr, "lrccs_batch_iterate: building the batch graph failed: %s", cudaGetErrorString(e));
+            return LRCCS_E_CUDA;
+        }
+        b->n_iter = n_iter;
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(nullptr, "lrccs_batch_iterate: graph launch failed");
+        return LRCCS_E_CUDA;
+    }
+    for (lrccs_ctx *c : b->ctxs) {
+        for (int k = 0; k < KID_COUNT; ++k) c->launches[k] += c->iter_counts[k];
+        c->t += n_iter;
+    }
+    return LRCCS_OK;
+}
+
+extern "C" void lrccs_batch_destroy(lrccs_batch *b) {
+    if (!b) return;
+    if (b->exec) {
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->exec);
+    }
+    delete b;
 }
 
 extern "C" lrccs_status lrccs_forward_transform(lrccs_ctx *c, void *d_T, size_t bytes) {

@@ -74,6 +74,8 @@ struct lrccs_ctx {
     // lrccs_iterate; rebuilt when the iteration count, the timed kernels or
     // the shape it was captured for change
     cudaGraphExec_t iter_exec;
+    cudaGraph_t iter_graph;             // the captured graph itself (a batch adds it as a child node)
+    unsigned long long iter_gen;        // bumped whenever the iteration graph is rebuilt
     long long iter_counts[KID_COUNT];   // kernel launches per replay
     std::vector<prof_rec> iter_prof;    // timing events recorded by the graph
     int iter_n, iter_r, iter_nused, iter_general, iter_nu;
@@ -109,6 +111,7 @@ struct lrccs_ctx {
     size_t create_bytes;   // device bytes allocated by lrccs_create
     async_worker *worker;  // started by the first lrccs_track_minibatch_async
     long long *d_gdts;     // lrccs_gdqr_phases: clock64() stamps of k_gdqr's blocks (NULL: off)
+    lrccs_plan plan;       // launch plan of the transform kernels (0 fields: defaults)
     std::string err;
 
     // geometry / sampling
@@ -237,6 +240,7 @@ cudaError_t launch_cg_init(lrccs_ctx *c, double *cg);
 cudaError_t launch_cg_step(lrccs_ctx *c, double *cg);
 cudaError_t launch_mean_resid(lrccs_ctx *c, const float2 *d_y, float2 *d_ytil, int nl_max);
 int npairs_of(int r);
+bool fwd_tile_ok(int tx, int r, int nx, int ny, int smem_optin);
 
 // Bits of the device status word ctx->d_status.
 enum {

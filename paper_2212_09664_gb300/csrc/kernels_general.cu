@@ -529,8 +529,9 @@ __global__ void k_mean_resid_gen(const float2 *__restrict__ y, const float2 *__r
 
 // ---------------------------------------------------------------- launchers
 
-static int row_groups(int nc) {   // coils per block of the row passes: about 4
-    const int cg = (nc + 3) / 4;
+static int row_groups(const lrccs_ctx *c) {   // coil groups of the row passes: about 4 coils each, or the plan's
+    if (c->plan.row_groups >= 1 && c->plan.row_groups <= 8 && c->plan.row_groups <= c->nc) return c->plan.row_groups;
+    const int cg = (c->nc + 3) / 4;
     return cg < 1 ? 1 : (cg > 8 ? 8 : cg);
 }
 
@@ -543,7 +544,7 @@ static const sw_t kSampleW[RMAXC] = RANK_TABLE(k_sample_w);
 cudaError_t launch_fwd_rows_r(lrccs_ctx *c, int r) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const size_t smem = ((size_t)2 * c->nx * r + c->nx) * sizeof(float2);
-    dim3 grid(c->n_used, row_groups(c->nc));
+    dim3 grid(c->n_used, row_groups(c));
     DISPATCH_P(c->px, {
         prof_begin(c, KID_FWD_ROWS);
         k_fwd_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_T, c->d_usedrows, c->d_uptr, c->d_uidx, c->d_FU, c->ny, r,
@@ -574,7 +575,7 @@ cudaError_t launch_sample_w(lrccs_ctx *c) {
 cudaError_t launch_adj_rows_r(lrccs_ctx *c, int r) {
     const float sx = (float)(1.0 / sqrt((double)c->nx));
     const size_t smem = ((size_t)c->nx * r + c->nx) * sizeof(float2);
-    dim3 grid(c->n_used, row_groups(c->nc));
+    dim3 grid(c->n_used, row_groups(c));
     DISPATCH_P(c->px, {
         prof_begin(c, KID_ADJ_ROWS);
         k_adj_rows<P_><<<grid, 256, smem, c->stream>>>(c->d_FU, c->d_usedrows, c->d_uptr, c->d_uidx, c->d_T, c->ny, r,

@@ -347,17 +347,25 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
 
 // ---------------------------------------------------------------- launchers
 
-// Columns per k_fwd_cols tile: even, and tx r <= 64 when possible.
-static int fwd_tile_x(int r, int nx) {
+// Columns per k_fwd_cols tile: even, and tx r <= 64 when possible; or the
+// context's tuned plan (lrccs_autotune / lrccs_set_plan) when it fits.
+bool fwd_tile_ok(int tx, int r, int nx, int ny, int smem_optin) {
+    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
+    return tx >= 2 && (tx & 1) == 0 && nx % tx == 0 && tx * r <= 256 && smem <= (size_t)smem_optin;
+}
+static int fwd_tile_x(const lrccs_ctx *c, int r) {
+    if (c->plan.fwd_tx && fwd_tile_ok(c->plan.fwd_tx, r, c->nx, c->ny, c->dev_smem_optin)) return c->plan.fwd_tx;
     int tx = 2;
-    while (tx * 2 * r <= 64 && tx * 2 <= nx) tx *= 2;
+    while (tx * 2 * r <= 64 && tx * 2 <= c->nx) tx *= 2;
     return tx;
 }
 
 // Coil groups (cluster size) of k_adj_cols, k_row_gram and k_row_w: groups of
-// about 4 coils, at most 8.
-static int adj_cluster(int nc) {
-    const int cg = (nc + 3) / 4;
+// about 4 coils, at most 8; or the tuned plan's.
+static int adj_cluster(const lrccs_ctx *c) {
+    if (c->plan.coil_groups >= 1 && c->plan.coil_groups <= 8 && c->plan.coil_groups <= c->nc)
+        return c->plan.coil_groups;
+    const int cg = (c->nc + 3) / 4;
     return cg < 1 ? 1 : (cg > 8 ? 8 : cg);
 }
 
@@ -373,7 +381,7 @@ static const row_w_t kRowW[RMAXC] = RANK_TABLE(k_row_w);
 cudaError_t launch_fwd_cols_on(lrccs_ctx *c, const float2 *src, int r) {
     const int nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
-    const int tx = fwd_tile_x(r, nx);
+    const int tx = fwd_tile_x(c, r);
     const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
     dim3 grid(nx / tx, c->nc);
     DISPATCH_P(c->py, {
@@ -388,7 +396,7 @@ cudaError_t launch_fwd_cols_on(lrccs_ctx *c, const float2 *src, int r) {
 static cudaError_t launch_row_gram(lrccs_ctx *c) {
     const int r = c->r, nx = c->nx, ny = c->ny;
     const size_t smem = (size_t)2 * nx * r * sizeof(float2);
-    const int cgr = adj_cluster(c->nc);
+    const int cgr = adj_cluster(c);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c->n_used, cgr, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -412,7 +420,7 @@ static void launch_row_w(lrccs_ctx *c) {
     const int r = c->r, nx = c->nx, ny = c->ny;
     const size_t smem = ((size_t)2 * nx * r + (size_t)c->q * r) * sizeof(float2);
     prof_begin(c, KID_ROW_W);
-    kRowW[r - 1]<<<dim3(c->n_used, adj_cluster(c->nc)), 256, smem, c->stream>>>(
+    kRowW[r - 1]<<<dim3(c->n_used, adj_cluster(c)), 256, smem, c->stream>>>(
         c->d_T, c->d_B, c->d_usedrows, c->d_rfptr, c->d_rflist, ny, nx, c->nc, c->q);
     prof_end(c, KID_ROW_W);
 }
@@ -422,7 +430,7 @@ cudaError_t launch_adj_cols_to(lrccs_ctx *c, float2 *dst, int r) {
     const int nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
     const size_t smem = ((size_t)4 * ny * r + 5 * (size_t)ny) * sizeof(float2);
-    const int cg = adj_cluster(c->nc);
+    const int cg = adj_cluster(c);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nx, cg, 1);
     cfg.blockDim = dim3(256, 1, 1);

@@ -38,6 +38,11 @@ class Params(C.Structure):
                 ("eta_scale0", C.c_double), ("eta_decay", C.c_double)]
 
 
+class Plan(C.Structure):
+    _fields_ = [("fwd_tx", C.c_int32), ("coil_groups", C.c_int32), ("row_groups", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class Ticket(C.Structure):
     _fields_ = [("id", C.c_uint64)]
 
@@ -75,6 +80,12 @@ _sig = {
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
     "lrccs_gdqr_phases": (_st, [_vp, C.c_int32, C.POINTER(C.c_double)]),
     "lrccs_forward_transform": (_st, [_vp, _vp, C.c_size_t]),
+    "lrccs_set_plan": (_st, [_vp, C.c_void_p]),
+    "lrccs_get_plan": (_st, [_vp, C.c_void_p]),
+    "lrccs_autotune": (_st, [_vp, C.c_int32, C.c_char_p, C.c_void_p]),
+    "lrccs_batch_create": (_st, [C.c_void_p, C.c_int32, _vp, C.POINTER(_vp)]),
+    "lrccs_batch_iterate": (_st, [_vp, C.c_int32]),
+    "lrccs_batch_destroy": (None, [_vp]),
     "lrccs_context_bytes": (_st, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "lrccs_track_minibatch_async": (_st, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _vp, C.c_void_p]),
     "lrccs_ticket_query": (_st, [_vp, C.c_void_p, C.POINTER(C.c_int32)]),
@@ -267,6 +278,39 @@ def lrccs_get_state(ctx) -> bytes:
 
 def lrccs_set_state(ctx, state: bytes):
     _check(ctx, _lib.lrccs_set_state(ctx, state, len(state)))
+
+
+def lrccs_set_plan(ctx, plan: Plan):
+    _check(ctx, _lib.lrccs_set_plan(ctx, C.byref(plan)))
+
+
+def lrccs_get_plan(ctx) -> Plan:
+    p = Plan()
+    _check(ctx, _lib.lrccs_get_plan(ctx, C.byref(p)))
+    return p
+
+
+def lrccs_autotune(ctx, n_iter: int = 5, cache_path: str = None) -> Plan:
+    p = Plan()
+    _check(ctx, _lib.lrccs_autotune(ctx, int(n_iter), None if cache_path is None else cache_path.encode(),
+                                    C.byref(p)))
+    return p
+
+
+def lrccs_batch_create(ctxs, stream=None):
+    arr = (_vp * len(ctxs))(*ctxs)
+    h = _vp()
+    s = None if stream is None else _vp(stream.cuda_stream)
+    _check(None, _lib.lrccs_batch_create(arr, len(ctxs), s, C.byref(h)))
+    return h.value
+
+
+def lrccs_batch_iterate(batch, n_iter: int):
+    _check(None, _lib.lrccs_batch_iterate(batch, int(n_iter)))
+
+
+def lrccs_batch_destroy(batch):
+    _lib.lrccs_batch_destroy(batch)
 
 
 def lrccs_forward_transform(ctx, T):
