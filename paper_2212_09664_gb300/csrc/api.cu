@@ -34,6 +34,7 @@ cudaError_t configure_kernels_iter(int max_smem);
 cudaError_t configure_kernels_gd(int max_smem);
 cudaError_t configure_kernels_general(int max_smem);
 cudaError_t configure_kernels_tc(int max_smem);
+cudaError_t configure_kernels_zh(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -84,7 +85,7 @@ static void free_all(lrccs_ctx *c) {
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
                     c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart,
-                    c->d_tflag, c->d_tcA0, c->d_tcA1, c->d_tcscale};
+                    c->d_tflag, c->d_tcA0, c->d_tcA1, c->d_tcscale, c->d_ZB, c->d_hpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -178,6 +179,7 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
         {(void **)&c->d_Up, (size_t)n * rmax * F2}, {(void **)&c->d_G, (size_t)n * rmax * F2},
         {(void **)&c->d_B, (size_t)q * rmax * F2}, {(void **)&c->d_P, (size_t)ny * npm * F2},
         {(void **)&c->d_gpart, gcap * F2}, {(void **)&c->d_tot, gd_len * sizeof(double2)},
+        {(void **)&c->d_ZB, (size_t)n * rmax * F2}, {(void **)&c->d_hpart, (size_t)uhz_grid_of(n) * q * rmax * F2},
         {(void **)&c->d_sigma, (size_t)q * D8}, {(void **)&c->d_gram, (size_t)6 * q * q * D8},
         {(void **)&c->d_V, (size_t)q * q * F2}, {(void **)&c->d_Q, (size_t)q * q * F2},
         {(void **)&c->d_framek, (size_t)q * ny * I4}, {(void **)&c->d_mks, (size_t)q * I4},
@@ -238,6 +240,7 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
     if (e == cudaSuccess) e = configure_kernels_gd(optin);
     if (e == cudaSuccess) e = configure_kernels_general(optin);
     if (e == cudaSuccess) e = configure_kernels_tc(optin);
+    if (e == cudaSuccess) e = configure_kernels_zh(optin);
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
@@ -448,8 +451,8 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
 }
 
 // U_0 <- the subspace in d_U (set from outside, or the previous mini-batch's
-// final U): one Cholesky QR pass of it (the init mode of k_gdqr, which also
-// forms the first B-step's right-hand sides U^H Z from the data now loaded).
+// final U): one Cholesky QR pass of it (the init mode of k_gdqr); the next
+// B-step forms its right-hand sides U^H Z from the data now loaded.
 static lrccs_status warm_start(lrccs_ctx *c) {
     const size_t ub = (size_t)c->n * c->r * sizeof(float2);
     CK(cudaMemcpyAsync(c->d_Up, c->d_U, ub, cudaMemcpyDeviceToDevice, c->stream));
@@ -1254,7 +1257,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale", "k_zb", "k_uhz"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -1364,7 +1367,7 @@ extern "C" lrccs_status lrccs_get_plan(lrccs_ctx *c, lrccs_plan *plan) {
 
 // The solver state one iteration reads and writes: U_t, U_{t-1}, B, the
 // scalars (step size, its schedule counter, SD) and the k_gdqr totals (the
-// right-hand sides U^H Z).
+// right-hand sides U^H Z are formed from U_t at every B-step).
 struct solver_state {
     std::vector<float2> U, Up, B;
     std::vector<double> scal;
@@ -1643,7 +1646,7 @@ extern "C" lrccs_status lrccs_forward_transform(lrccs_ctx *c, void *d_T, size_t 
 
 extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *out) {
     if (!c) return LRCCS_E_INVALID;
-    const int G = c->gd_grid, NTS = 12;
+    const int G = c->gd_grid, NTS = 9;   // the stamps of k_gdqr (GD_NTS)
     if (out) {
         if (!c->d_gdts) {
             set_err(c, "lrccs_gdqr_phases: phase timing is off");

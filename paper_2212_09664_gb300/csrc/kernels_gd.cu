@@ -2,15 +2,15 @@
 // one cooperative kernel (one block per SM, every block resident):
 //
 //   phase 1  grad = Gk - Z B^H  (Gk = sum_j conj(d_j) F^H K_j from the adjoint
-//            transforms), partial sums of grad^H grad, U^H grad, U^H U
+//            transforms, Z B^H from k_zb), partial sums of grad^H grad,
+//            U^H grad, U^H U
 //   -------  grid reduction; every block: eta = eta_c / ||grad||_2 (t = 1),
 //            G1 = (U - eta grad)^H (U - eta grad)
 //                = U^H U - eta (U^H grad + grad^H U) + eta^2 grad^H grad,
 //            G1 = R1^H R1 (Cholesky), R1^{-1}
 //   phase 2  U_{t+1} = (U - eta grad) R1^{-1}  (the QR step of Alg. 2 as
-//            Cholesky QR), partial sums of U_t^H U_{t+1} (for SD) and
-//            U_{t+1}^H Z (the next B-step's right-hand sides h_k = U^H Z[:, k])
-//   -------  grid reduction; the last block out computes SD(U_t, U_{t+1}).
+//            Cholesky QR), pixel by pixel; the last block out forms
+//            SD(U_t, U_{t+1}) from U_t^H U_{t+1} = (U^H U - eta U^H grad) R1^{-1}.
 //
 // G1 is formed from the exact U^H U of the current (FP32) iterate, so each
 // iteration removes the loss of orthogonality of the previous one; with
@@ -20,6 +20,10 @@
 // In init mode the same kernel orthonormalises the given U+ (G1 = U+^H U+).
 // A block's pixel range stays in shared memory across the phases when it
 // fits; otherwise each phase re-stages it in chunks.
+//
+// The two contractions with Z = [A_k^H y_k] run as their own pixel-parallel
+// kernels: k_zb (Z B^H, after the B-step) and k_uhz (the B-step's right-hand
+// sides U^H Z, partial sums per block, added up by the solve).
 //
 // Partial sums are FP32 within a block and FP64 across blocks, reduced in a
 // fixed order (deterministic).  The grid barriers spin on a global counter
@@ -31,13 +35,11 @@
 #include "internal.h"
 
 #define RMAXC 16   // compile-time bound on the rank
-#define QMAXC 128  // compile-time bound on the number of frames
 #define NTG 512    // threads per block
 
 struct GdArgs {
     const float2 *Gk;   // n x r   sum_j conj(d_j) F^H K_j (iteration mode)
-    const float2 *Z;    // n x q   A_k^H y_k, row-major (i q + k)
-    const float2 *B;    // q x r   B_t (row k = b_k)
+    const float2 *ZB;   // n x r   Z B^H (iteration mode)
     float2 *U;          // n x r   U_t in, U_{t+1} out
     float2 *Uprev;      // n x r   receives U_t (iteration mode)
     const float2 *Up;   // n x r   U+ (init mode)
@@ -47,7 +49,7 @@ struct GdArgs {
     double *scal;       // SC_* scalars
     unsigned int *bar;  // [0] barrier arrivals, [1] exit count
     unsigned int *status;
-    int n, r, q, zs, chunk, resident, mode;
+    int n, r, chunk, resident, mode;
     double eta_c;
     double eta_scale0, eta_decay;   // variable step size: eta_t = eta eta_scale0 eta_decay^k
     long long *ts;             // NULL, or GD_NTS clock64() stamps per block (phase timing)
@@ -57,7 +59,7 @@ struct GdArgs {
 
 // Phase timing (measurement support): thread 0 of every block stamps clock64()
 // at GD_NTS points of the kernel when a.ts is set.
-#define GD_NTS 12
+#define GD_NTS 9
 #define GD_TS(i)                                                                    \
     do {                                                                            \
         if (a.ts && threadIdx.x == 0) a.ts[(size_t)blockIdx.x * GD_NTS + (i)] = clock64(); \
@@ -247,12 +249,10 @@ template <int R>
 __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     extern __shared__ __align__(16) float2 smem[];
     constexpr int r = R;
-    const int q = a.q, zs = a.zs, chunk = a.chunk;
+    const int chunk = a.chunk;
     float2 *s_u = smem;                 // chunk * r : U_t (iteration) or U+ (init)
     float2 *s_a = s_u + chunk * r;      // chunk * r : Gk, grad, then U_{t+1}
-    float2 *s_w = s_a + chunk * r;      // chunk * r : U - eta grad
-    float2 *s_z = s_w + chunk * r;      // chunk * zs: Z
-    __shared__ __align__(16) float2 sB[QMAXC * R];
+    float2 *s_w = s_a + chunk * r;      // chunk * r : Z B^H, then U - eta grad
     __shared__ float2 sL[R * R];
     __shared__ float2 sR[R * R];
     __shared__ float sinv[R];
@@ -315,71 +315,27 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         for (int m = 0; m < 4; ++m) acc[u][m] = make_float2(0.f, 0.f);
     }
     GD_TS(0);
-    if (iter)
-        for (int e = t; e < q * r; e += NTG) cp_async8(sB + e, a.B + e);
     for (int c0 = i0; c0 < i1; c0 += chunk) {
         const int cn = min(chunk, i1 - c0);
         __syncthreads();
         if (iter) {
             stage_rows(s_a, r, a.Gk + (size_t)c0 * r, r, cn, r);
             stage_rows(s_u, r, a.U + (size_t)c0 * r, r, cn, r);
+            stage_rows(s_w, r, a.ZB + (size_t)c0 * r, r, cn, r);
         } else {
             stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
         }
-        stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
         cp_async_commit();
         cp_async_wait();
         __syncthreads();
         if (c0 == i0) GD_TS(1);
-        if (iter) {
-            // grad = Gk - Z B^H.  Thread = (pixel pair pp, part kq of the k range,
-            // NQ = NTG / 128 parts); the parts are subtracted from Gk in the fixed
-            // order NQ - 1, ..., 1, 0.
-            constexpr int NQ = NTG / 128;
-            const int pp = t & 127, kq = t >> 7;
-            const int K4 = ((q + 2 * NQ - 1) / (2 * NQ)) * 2;
-            const int k0 = min(q, kq * K4), k1 = min(q, k0 + K4);
-            const int p0 = min(2 * pp, cn - 1), p1 = min(2 * pp + 1, cn - 1);
-            float2 g0[R], g1v[R];
-#pragma unroll
-            for (int l = 0; l < R; ++l) g0[l] = g1v[l] = make_float2(0.f, 0.f);
-            const float2 *z0r = s_z + p0 * zs, *z1r = s_z + p1 * zs;
-            int k = k0;
-#pragma unroll(R <= 12 ? 2 : 1)
-            for (; k + 1 < k1; k += 2) {
-                const float4 za = *(const float4 *)(z0r + k), zb = *(const float4 *)(z1r + k);
-#pragma unroll
-                for (int l = 0; l < R; ++l) {   // g += z_k conj(b_k[l]) + z_{k+1} conj(b_{k+1}[l])
-                    const float2 b0 = sB[k * r + l], b1 = sB[(k + 1) * r + l];
-                    g0[l].x = fmaf(za.x, b0.x, fmaf(za.y, b0.y, fmaf(za.z, b1.x, fmaf(za.w, b1.y, g0[l].x))));
-                    g0[l].y = fmaf(za.y, b0.x, fmaf(-za.x, b0.y, fmaf(za.w, b1.x, fmaf(-za.z, b1.y, g0[l].y))));
-                    g1v[l].x = fmaf(zb.x, b0.x, fmaf(zb.y, b0.y, fmaf(zb.z, b1.x, fmaf(zb.w, b1.y, g1v[l].x))));
-                    g1v[l].y = fmaf(zb.y, b0.x, fmaf(-zb.x, b0.y, fmaf(zb.w, b1.x, fmaf(-zb.z, b1.y, g1v[l].y))));
-                }
+        if (iter) {   // grad = Gk - Z B^H
+            for (int e = t; e < cn * r; e += NTG) {
+                const float2 g = csub(s_a[e], s_w[e]);
+                s_a[e] = g;
+                a.Gr[(size_t)c0 * r + e] = g;
             }
-            if (k < k1) {
-                const float2 za = z0r[k], zb = z1r[k];
-#pragma unroll
-                for (int l = 0; l < R; ++l) {
-                    const float2 b0 = sB[k * r + l];
-                    g0[l].x = fmaf(za.x, b0.x, fmaf(za.y, b0.y, g0[l].x));
-                    g0[l].y = fmaf(za.y, b0.x, fmaf(-za.x, b0.y, g0[l].y));
-                    g1v[l].x = fmaf(zb.x, b0.x, fmaf(zb.y, b0.y, g1v[l].x));
-                    g1v[l].y = fmaf(zb.y, b0.x, fmaf(-zb.x, b0.y, g1v[l].y));
-                }
-            }
-            const bool v0 = 2 * pp < cn, v1 = 2 * pp + 1 < cn;
-            for (int qq = NQ - 1; qq >= 0; --qq) {
-                if (kq == qq) {
-#pragma unroll
-                    for (int l = 0; l < R; ++l) {
-                        if (v0) s_a[p0 * r + l] = csub(s_a[p0 * r + l], g0[l]);
-                        if (v1) s_a[p1 * r + l] = csub(s_a[p1 * r + l], g1v[l]);
-                    }
-                }
-                __syncthreads();
-            }
-            for (int e = t; e < cn * r; e += NTG) a.Gr[(size_t)c0 * r + e] = s_a[e];
+            __syncthreads();
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u)
@@ -477,19 +433,6 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     const float etaf = iter ? s_eta : 0.f;
 
     // ------------------------------------------------ phase 2: U_{t+1} = (U - eta grad) R1^{-1}
-    // partial sums, all R columns per thread:
-    //   h-threads  t < Hth:           (k pair kp, slice s): conj(U_{t+1}[l]) Z[2kp + j]
-    //   C-threads  Hth <= t < Hth+Cth: (row x, slice s):    conj(U_t[x]) U_{t+1}[y]
-    const int tq = (q + 1) >> 1;
-    const int len2 = rr + q * r;
-    const int Sc = max(1, 64 / R), Cth = R * Sc;
-    const int Sh = max(1, (NTG - Cth) / tq), Hth = tq * Sh;
-    const bool hthr = t < Hth, cthr = !hthr && t < Hth + Cth;
-    const int hk = 2 * (t % tq), hs = t / tq;
-    const int cx = (t - Hth) % R, cs = (t - Hth) / R;
-    float2 pv[2 * R];
-#pragma unroll
-    for (int v = 0; v < 2 * R; ++v) pv[v] = make_float2(0.f, 0.f);
     for (int c0 = i0; c0 < i1; c0 += chunk) {
         const int cn = min(chunk, i1 - c0);
         if (!a.resident) {
@@ -500,7 +443,6 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             } else {
                 stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
             }
-            stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
             cp_async_commit();
             cp_async_wait();
         }
@@ -513,75 +455,15 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
 #pragma unroll
             for (int m = 0; m < R; ++m)
                 if (m <= l) cfma(v, s_w[ii * r + m], sR[m * r + l]);
-            s_a[e] = v;
-        }
-        __syncthreads();
-        for (int e = t; e < cn * r; e += NTG) {
-            a.U[(size_t)c0 * r + e] = s_a[e];
+            a.U[(size_t)c0 * r + e] = v;
             if (iter) a.Uprev[(size_t)c0 * r + e] = s_u[e];
-        }
-        if (hthr) {
-#pragma unroll(R <= 12 ? 2 : 1)
-            for (int ii = hs; ii < cn; ii += Sh) {
-                const float4 z = *(const float4 *)(s_z + ii * zs + hk);   // Z[k], Z[k+1] (pad column when k+1 = q)
-                const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
-#pragma unroll
-                for (int l = 0; l < R; ++l) {
-                    const float2 u = s_a[ii * r + l];
-                    cfmac(pv[l], u, z0);
-                    cfmac(pv[R + l], u, z1);
-                }
-            }
-        } else if (cthr) {
-#pragma unroll(R <= 12 ? 2 : 1)
-            for (int ii = cs; ii < cn; ii += Sc) {
-                const float2 ux = s_u[ii * r + cx];
-#pragma unroll
-                for (int y = 0; y < R; ++y) cfmac(pv[y], ux, s_a[ii * r + y]);
-            }
         }
     }
     GD_TS(8);
-    // partial row: [U_t^H U_{t+1} (rr, x r + y) | h (q r, k r + l)]; slices summed in
-    // order, V values per thread per round (s_w and s_z are free after the last chunk)
-    {
-        const int cap2 = chunk * (r + zs);
-        float2 *scr = cap2 >= 2 * NTG ? s_w : s_red2;
-        const int V = max(2, min(2 * R, ((cap2 >= 2 * NTG ? cap2 : 2 * NTG) / NTG) & ~1));
-        for (int v0 = 0; v0 < 2 * R; v0 += V) {
-            __syncthreads();
-            if (hthr || cthr) {
-#pragma unroll
-                for (int v = 0; v < 2 * R; ++v)
-                    if (v >= v0 && v < v0 + V && (hthr || v < R)) scr[(v - v0) * NTG + t] = pv[v];
-            }
-            __syncthreads();
-            const int vn = min(V, 2 * R - v0);
-            for (int w = t; w < vn * (tq + R); w += NTG) {
-                const int dv = w / (tq + R), rem = w - dv * (tq + R), v = v0 + dv;
-                if (rem < tq) {
-                    const int kp = rem, k = 2 * kp + v / R, l = v % R;
-                    if (k < q) {
-                        float2 sum = make_float2(0.f, 0.f);
-                        for (int ss = 0; ss < Sh; ++ss) sum = cadd(sum, scr[dv * NTG + ss * tq + kp]);
-                        a.part[(size_t)blockIdx.x * len2 + rr + k * r + l] = sum;
-                    }
-                } else if (v < R) {
-                    const int x = rem - tq;
-                    float2 sum = make_float2(0.f, 0.f);
-                    for (int ss = 0; ss < Sc; ++ss) sum = cadd(sum, scr[dv * NTG + Hth + ss * R + x]);
-                    a.part[(size_t)blockIdx.x * len2 + x * r + v] = sum;
-                }
-            }
-        }
-    }
-    GD_TS(9);
-    grid_sync(a.bar, 3, a.status, a.spin_limit, a.bar_skew);
-    GD_TS(10);
-    grid_reduce(a.part, len2, a.tot);
-    GD_TS(11);
-    // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2, and
-    // the barrier counters back to zero (every block is past its last barrier)
+    // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2 with
+    // U_t^H U_{t+1} = (U_t^H U_t - eta U_t^H grad) R1^{-1} from the FP64 totals
+    // (no second reduction), and the barrier counters back to zero (every block
+    // is past its last barrier)
     __syncthreads();
     if (t == 0) {
         __threadfence();
@@ -590,12 +472,25 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     }
     __syncthreads();
     if (!s_flag) return;
-    __threadfence();
     if (t < 32) {
         double sum = 0.0;
-        for (int e = t; e < rr; e += 32) {
-            const double2 v = __ldcg(a.tot + e);
-            sum += v.x * v.x + v.y * v.y;
+        if (iter) {
+            const double etad = (double)etaf;
+            for (int e = t; e < rr; e += 32) {
+                const int x = e / r, y = e - x * r;
+                double mr = 0.0, mi = 0.0;
+                for (int m = 0; m <= y; ++m) {
+                    const int p = x <= m ? pair_index(x, m, r) : pair_index(m, x, r);
+                    const double2 uu = __ldcg(a.tot + np + rr + p);
+                    const double2 ug = __ldcg(a.tot + np + x * r + m);
+                    const double cr = uu.x - etad * ug.x;
+                    const double ci = (x <= m ? uu.y : -uu.y) - etad * ug.y;
+                    const float2 q = sR[m * r + y];
+                    mr += cr * (double)q.x - ci * (double)q.y;
+                    mi += cr * (double)q.y + ci * (double)q.x;
+                }
+                sum += mr * mr + mi * mi;
+            }
         }
         sum = warp_sum_d(sum);
         if (t == 0) {
@@ -606,6 +501,118 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             a.bar[0] = 0u;
             a.bar[1] = 0u;
         }
+    }
+}
+
+// ---------------------------------------------------------------- Z contractions
+
+// Z B^H (n x r): ZB[i][l] = sum_k Z[i][k] conj(B[k][l]), the data term of the
+// gradient grad = Gk - Z B^H (Alg. 2).  Block = ZB_PIX pixels, thread = (pixel,
+// half of the l range); the pixels' Z rows are staged with an odd row stride
+// (conflict-free 8-byte loads across pixels), B is read by broadcast.
+#define ZB_PIX 128
+template <int R>
+__global__ void __launch_bounds__(256) k_zb(const float2 *__restrict__ Z, const float2 *__restrict__ B, int n, int q,
+                                            float2 *__restrict__ ZB) {
+    extern __shared__ __align__(16) float2 smem[];
+    constexpr int RH = (R + 1) / 2;
+    const int zs = q | 1;
+    float2 *s_z = smem;               // ZB_PIX * zs
+    float2 *s_b = s_z + ZB_PIX * zs;  // q * R
+    const int i0 = blockIdx.x * ZB_PIX, cn = min(ZB_PIX, n - i0);
+    for (int e = threadIdx.x; e < cn * q; e += blockDim.x) {
+        const int ii = e / q, k = e - ii * q;
+        cp_async8(s_z + ii * zs + k, Z + (size_t)i0 * q + e);
+    }
+    for (int e = threadIdx.x; e < q * R; e += blockDim.x) cp_async8(s_b + e, B + e);
+    cp_async_commit();
+    cp_async_wait();
+    __syncthreads();
+    const int p = threadIdx.x & (ZB_PIX - 1), h = threadIdx.x / ZB_PIX;
+    if (p >= cn) return;
+    const int l0 = h * RH, nl = min(RH, R - l0);
+    float2 acc[RH];
+#pragma unroll
+    for (int j = 0; j < RH; ++j) acc[j] = make_float2(0.f, 0.f);
+    const float2 *zr = s_z + p * zs;
+#pragma unroll 4
+    for (int k = 0; k < q; ++k) {
+        const float2 z = zr[k];
+#pragma unroll
+        for (int j = 0; j < RH; ++j)
+            if (j < nl) cfmac(acc[j], s_b[k * R + l0 + j], z);   // conj(b) z
+    }
+#pragma unroll
+    for (int j = 0; j < RH; ++j)
+        if (j < nl) ZB[(size_t)(i0 + p) * R + l0 + j] = acc[j];
+}
+
+// Partial sums of h = U^H Z (r x q, the B-step's right-hand sides h_k =
+// (A_k U)^H y_k = U^H Z[:, k], Alg. 2) over the block's UH_PIX pixels:
+// hpart[b][k r + l] = sum_i conj(U[i][l]) Z[i][k].  Thread = (pair of frames,
+// slice of the pixels); the slices are added in a fixed order.  The per-frame
+// totals are formed by the B-step's solve, which adds the blocks' rows in order.
+#define UH_PIX 128
+template <int R>
+__global__ void __launch_bounds__(256) k_uhz(const float2 *__restrict__ U, const float2 *__restrict__ Z, int n, int q,
+                                             float2 *__restrict__ hpart) {
+    extern __shared__ __align__(16) float2 smem[];
+    const int zs = ((q + 1) | 3) - 1;   // even, 2 mod 4: 16-byte loads of consecutive frame pairs
+    float2 *s_z = smem;                 // UH_PIX * zs
+    float2 *s_u = s_z + UH_PIX * zs;    // UH_PIX * R
+    const int i0 = blockIdx.x * UH_PIX, cn = min(UH_PIX, n - i0);
+    const int t = threadIdx.x;
+    if ((q & 1) == 0) {
+        const int h = q >> 1;
+        for (int e = t; e < cn * h; e += blockDim.x) {
+            const int ii = e / h, c2 = e - ii * h;
+            cp_async16(s_z + ii * zs + 2 * c2, Z + (size_t)(i0 + ii) * q + 2 * c2);
+        }
+    } else {
+        for (int e = t; e < cn * q; e += blockDim.x) {
+            const int ii = e / q, k = e - ii * q;
+            cp_async8(s_z + ii * zs + k, Z + (size_t)i0 * q + e);
+        }
+    }
+    for (int e = t; e < cn * R; e += blockDim.x) cp_async8(s_u + e, U + (size_t)i0 * R + e);
+    cp_async_commit();
+    cp_async_wait();
+    __syncthreads();
+    if (q & 1)   // the pad column read with the last frame pair
+        for (int ii = t; ii < cn; ii += blockDim.x) s_z[ii * zs + q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int tq = (q + 1) >> 1, S = max(1, (int)blockDim.x / tq);
+    const int kp = t % tq, s = t / tq, k = 2 * kp;
+    float2 pv[2 * R];
+#pragma unroll
+    for (int v = 0; v < 2 * R; ++v) pv[v] = make_float2(0.f, 0.f);
+    if (s < S) {
+#pragma unroll 2
+        for (int ii = s; ii < cn; ii += S) {
+            const float4 z = *(const float4 *)(s_z + ii * zs + k);
+            const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
+#pragma unroll
+            for (int l = 0; l < R; ++l) {
+                const float2 u = s_u[ii * R + l];
+                cfmac(pv[l], u, z0);
+                cfmac(pv[R + l], u, z1);
+            }
+        }
+    }
+    // slices in order: the staging area is free now (2 R values per thread)
+    __syncthreads();
+    float2 *scr = smem;   // 2 R blockDim.x <= UH_PIX (zs + R) for every q >= 1, R <= 16
+    if (s < S) {
+#pragma unroll
+        for (int v = 0; v < 2 * R; ++v) scr[v * blockDim.x + t] = pv[v];
+    }
+    __syncthreads();
+    for (int o = t; o < q * R; o += blockDim.x) {
+        const int kk = o / R, l = o - kk * R;
+        const int v = (kk & 1) * R + l, kpp = kk >> 1;
+        float2 sum = make_float2(0.f, 0.f);
+        for (int ss = 0; ss < S; ++ss) sum = cadd(sum, scr[v * blockDim.x + ss * tq + kpp]);
+        hpart[(size_t)blockIdx.x * q * R + o] = sum;
     }
 }
 
@@ -630,25 +637,19 @@ cudaError_t configure_kernels_gd(int max_smem) {
     return cudaSuccess;
 }
 
-// Z row stride in shared memory: q rounded up to 2 mod 4 complex values, so
-// that 16-byte loads of consecutive pixels' rows hit distinct banks.
-static int z_stride(int q) { return ((q + 1) | 3) - 1; }
-
 cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
-    const int r = c->r, q = c->q, G = c->gd_grid;
+    const int r = c->r, G = c->gd_grid;
     if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
-    const int zs = z_stride(q);
     const int per = (c->n + G - 1) / G;
-    const size_t bpp = (size_t)(3 * r + zs) * sizeof(float2);
+    const size_t bpp = (size_t)3 * r * sizeof(float2);
     const size_t avail = (size_t)(c->dev_smem_optin - g_gd_static_smem[r - 1]);
     int chunk = (int)(avail / bpp) & ~1;
-    chunk = min(chunk, 256);
+    chunk = min(chunk, 512);
     chunk = min(chunk, (per + 1) & ~1);
     if (chunk < 2) return cudaErrorInvalidConfiguration;
     GdArgs a;
     a.Gk = c->d_Up;
-    a.Z = c->d_Z;
-    a.B = c->d_B;
+    a.ZB = c->d_ZB;
     a.U = c->d_U;
     a.Uprev = c->d_Uprev;
     a.Up = c->d_Up;
@@ -660,8 +661,6 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.status = c->d_status;
     a.n = c->n;
     a.r = r;
-    a.q = q;
-    a.zs = zs;
     a.chunk = chunk;
     a.resident = chunk >= per ? 1 : 0;
     a.mode = mode;
@@ -682,4 +681,51 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kGd[r - 1], dim3(G), dim3(NTG), args, smem, c->stream);
     prof_end(c, KID_GDQR);
     return e;
+}
+
+typedef void (*zb_kernel_t)(const float2 *, const float2 *, int, int, float2 *);
+#define RANK_TABLE(K) {K<1>, K<2>, K<3>, K<4>, K<5>, K<6>, K<7>, K<8>, K<9>, K<10>, K<11>, K<12>, K<13>, K<14>, K<15>, K<16>}
+static const zb_kernel_t kZb[RMAXC] = RANK_TABLE(k_zb);
+static const zb_kernel_t kUhz[RMAXC] = RANK_TABLE(k_uhz);
+
+static size_t zb_smem(int q, int r) { return ((size_t)ZB_PIX * (q | 1) + (size_t)q * r) * sizeof(float2); }
+static size_t uhz_smem(int q, int r) {
+    const size_t stage = (size_t)UH_PIX * ((((q + 1) | 3) - 1) + r), scr = (size_t)2 * r * 256;
+    return (stage > scr ? stage : scr) * sizeof(float2);
+}
+int uhz_grid_of(int n) { return (n + UH_PIX - 1) / UH_PIX; }
+
+// d_ZB <- Z B^H (the data term of the next gradient), from the current B.
+cudaError_t launch_zb(lrccs_ctx *c) {
+    const int r = c->r;
+    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
+    prof_begin(c, KID_ZB);
+    kZb[r - 1]<<<(c->n + ZB_PIX - 1) / ZB_PIX, 256, zb_smem(c->q, r), c->stream>>>(c->d_Z, c->d_B, c->n, c->q,
+                                                                                   c->d_ZB);
+    prof_end(c, KID_ZB);
+    return cudaGetLastError();
+}
+
+// d_hpart <- per-block partial sums of U^H Z at the current U (the B-step's
+// right-hand sides; the solve adds the uhz_grid_of(n) rows per frame).
+cudaError_t launch_uhz(lrccs_ctx *c) {
+    const int r = c->r;
+    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
+    prof_begin(c, KID_UHZ);
+    kUhz[r - 1]<<<uhz_grid_of(c->n), 256, uhz_smem(c->q, r), c->stream>>>(c->d_U, c->d_Z, c->n, c->q, c->d_hpart);
+    prof_end(c, KID_UHZ);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_kernels_zh(int max_smem) {
+    for (int i = 0; i < RMAXC; ++i) {
+        const int r = i + 1;
+        const size_t a = zb_smem(128, r), b = uhz_smem(128, r);   // the largest q
+        if ((int)a > max_smem || (int)b > max_smem) return cudaErrorInvalidConfiguration;
+        cudaError_t e = cudaFuncSetAttribute(kZb[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kUhz[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
