@@ -41,7 +41,7 @@ T_ITER = 50
 METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
 UNIT = "frame-iterations/s"
 FLUSH_BYTES = 256 << 20            # > 129 MB L2
-ITER_KERNELS = ["k_uhz", "k_fwd_cols", "k_row_gram", "k_solve", "k_zb", "k_row_w", "k_adj_cols", "k_gdqr"]
+ITER_KERNELS = ["k_fwd_cols", "k_row_gram", "k_solve", "k_zb", "k_row_w", "k_adj_cols", "k_gdqr"]
 
 
 def dist_env():
@@ -88,9 +88,8 @@ def kernel_bytes(name, p, r, n_used):
         "k_row_gram": C * r * nu,                        # read the sampled rows
         "k_row_w": 2 * C * r * nu,                       # read the sampled rows, write T W (in place)
         "k_adj_cols": C * r * nu + C * n + n * r,        # read rows, d_j; write sum_j conj(d_j) F^H K_j
-        "k_gdqr": 6 * n * r,                             # read that, U, Z B^H; write grad, U_{t+1}, U_t
+        "k_gdqr": 6 * n * r + n * q,                     # read that, U, Z B^H, Z; write grad, U_{t+1}, U_t
         "k_zb": n * q + n * r,                           # read Z (B is tiny); write Z B^H
-        "k_uhz": n * q + n * r,                          # read Z, U (the per-block partial sums are tiny)
         "k_solve": 0,
     }.get(name, 0)
     return 8 * b
@@ -476,9 +475,7 @@ def library_comparators(p, dev, used_rows, stats):
                 sampled rows                         vs k_fwd_cols
       adjoint : scatter of the sampled rows, inverse FFT along ky (cuFFT),
                 conj(d_j) multiply, coil sum          vs k_adj_cols
-      gemms   : the iteration's skinny products Z B^H and U^H Z (cuBLAS)
-                vs k_zb + k_uhz (U^H Z as per-block partial sums, which
-                the solve adds up)
+      zb      : the gradient's skinny product Z B^H (cuBLAS) vs k_zb
     Times are CUDA-event averages over back-to-back launches (inputs resident,
     as for the kernels' own event times taken during the warm-up solves)."""
     import torch
@@ -503,9 +500,6 @@ def library_comparators(p, dev, used_rows, stats):
         G = torch.fft.ifft(full, dim=2, norm="ortho")
         return (S.conj()[:, None] * G).sum(0)
 
-    def gemms():
-        return Z @ Bm.conj(), U.reshape(n, r).conj().transpose(0, 1) @ Z
-
     def time_us(fn, reps=50):
         for _ in range(5):
             fn()
@@ -527,9 +521,8 @@ def library_comparators(p, dev, used_rows, stats):
                      library="torch elementwise + cuFFT (torch.fft.fft) + index_select"),
         adjoint=dict(library_us=time_us(adjoint), lrccs_kernel="k_adj_cols", lrccs_us=ours_us("k_adj_cols"),
                      library="index_copy + cuFFT (torch.fft.ifft) + elementwise + sum"),
-        gemms=dict(library_us=time_us(gemms), lrccs_kernel="k_zb + k_uhz",
-                   lrccs_us=(ours_us("k_zb") or 0.0) + (ours_us("k_uhz") or 0.0),
-                   library="cuBLAS (torch.matmul): Z B^H and U^H Z"))
+        zb=dict(library_us=time_us(lambda: Z @ Bm.conj()), lrccs_kernel="k_zb", lrccs_us=ours_us("k_zb"),
+                library="cuBLAS (torch.matmul): Z B^H"))
     del full, K, Z, U
     torch.cuda.empty_cache()
     return out
@@ -615,12 +608,12 @@ def radial_leg(dev, stream, steps=5, warmup=3):
     n, q, C, r = p.n, p.q, p.nc, p.rank
     # algorithmic bytes of one general-mask iteration (complex64 = 8 B): U, maps
     # and the rows of T (fwd_cols); T in, FU out (fwd_rows); FU (Grams); FU in
-    # and out (W); FU in, T out (adj_rows); T, maps in, Gk out (adj_cols); k_gdqr,
-    # k_zb and k_uhz
+    # and out (W); FU in, T out (adj_rows); T, maps in, Gk out (adj_cols); k_gdqr
+    # and k_zb
     rows = int(p.mask.reshape(q, p.ny, p.nx).any(2).any(0).sum())
     t_rows = C * r * rows * p.nx
     it_bytes = 8 * ((n * r + C * n + t_rows) + (t_rows + C * r * nu) + C * r * nu + 2 * C * r * nu
-                    + (C * r * nu + t_rows) + (t_rows + C * n + n * r) + 6 * n * r + 2 * (n * q + n * r))
+                    + (C * r * nu + t_rows) + (t_rows + C * n + n * r) + (6 * n * r + n * q) + (n * q + n * r))
     peak, peak_kind = peaks()
     per_kernel = {d["name"]: d["ms"] / d["timed"] * 1e3 for d in stats if d["timed"] > 0 and d["launches"] > 0}
     s.close()

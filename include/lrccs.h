@@ -446,7 +446,7 @@ lrccs_status lrccs_get_plan(lrccs_ctx *ctx, lrccs_plan *plan);
  * 8, 16, 32}, coil_groups in {1, 2, 3, 4, 6, 8} and, for general masks,
  * row_groups in {1, 2, 4, 8}, each within the shape's limits, one field at a
  * time from the defaults -- applies the fastest, and restores the solver
- * state (U, U_{t-1}, B, step size and its schedule), so the solve continues
+ * state (U, U_{t-1}, B, step size and its schedule, right-hand sides), so the solve continues
  * exactly as if it had not been tuned.  cache_path (NULL: no cache) names a
  * text file of tuned plans, one line per shape (ny nx q C r mask-kind
  * precision fwd_tx coil_groups row_groups): a shape found there is applied
@@ -480,13 +480,15 @@ lrccs_status lrccs_forward_transform(lrccs_ctx *ctx, void *d_T, size_t bytes);
 
 /* Phase timing of the GD/QR kernel (measurement support, like the paper's
  * per-step timing markers, Sec. V).  enable != 0 allocates a stamp buffer and
- * makes every later directly launched GD/QR kernel (one-iteration
- * lrccs_iterate calls; not graph replays) record clock64() at 9 points in
- * each block: start, inputs staged, gradient and Gram partials done, partials
- * written, grid barrier 1 passed, totals reduced, barrier 2 passed, the r x r
- * factors done, U_{t+1} written.  out (NULL, or 16 doubles) receives, for
- * each of the 8 intervals, the mean and the maximum over the blocks in SM
- * cycles of the last such launch.  enable == 0 with out == NULL frees the buffer.
+ * makes every later GD/QR kernel of an iteration (launched directly or
+ * replayed in the iteration graph, which is re-captured) record clock64() at
+ * 9 points in each block: start, inputs staged, gradient and Gram partials
+ * done, partials written, grid barrier 1 passed, totals reduced, barrier 2
+ * passed, the r x r factors done, U_{t+1} written; and the global timer at
+ * the block's entry and exit.  out (NULL, or 18 doubles) receives, for each of
+ * the 8 intervals, the mean and the maximum over the blocks in SM cycles of
+ * the last such launch, then the time from the first block's entry to the
+ * last block's exit and the spread of the entries, in ns.  enable == 0 with out == NULL frees the buffer.
  * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (out requested while off), LRCCS_E_NOMEM. */
 lrccs_status lrccs_gdqr_phases(lrccs_ctx *ctx, int32_t enable, double *out);
 

@@ -78,6 +78,12 @@ extern "C" const char *lrccs_status_string(lrccs_status s) {
 extern "C" const char *lrccs_last_error(const lrccs_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 static void free_all(lrccs_ctx *c) {
+    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
+    c->side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     void *ptrs[] = {c->d_twy, c->d_twx, c->d_smaps, c->d_rowcnt, c->d_rowidx, c->d_framerows, c->d_lineptr,
                     c->d_rfptr, c->d_rflist, c->d_usedrows, c->d_rowused, c->d_idx, c->d_meta, c->d_status,
                     c->d_counters, c->d_scal, c->d_Z, c->d_X0, c->d_T, c->d_U, c->d_Uprev, c->d_Up, c->d_G,
@@ -179,7 +185,7 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
         {(void **)&c->d_Up, (size_t)n * rmax * F2}, {(void **)&c->d_G, (size_t)n * rmax * F2},
         {(void **)&c->d_B, (size_t)q * rmax * F2}, {(void **)&c->d_P, (size_t)ny * npm * F2},
         {(void **)&c->d_gpart, gcap * F2}, {(void **)&c->d_tot, gd_len * sizeof(double2)},
-        {(void **)&c->d_ZB, (size_t)n * rmax * F2}, {(void **)&c->d_hpart, (size_t)uhz_grid_of(n) * q * rmax * F2},
+        {(void **)&c->d_ZB, (size_t)n * rmax * F2}, {(void **)&c->d_hpart, (size_t)gd * q * rmax * F2},
         {(void **)&c->d_sigma, (size_t)q * D8}, {(void **)&c->d_gram, (size_t)6 * q * q * D8},
         {(void **)&c->d_V, (size_t)q * q * F2}, {(void **)&c->d_Q, (size_t)q * q * F2},
         {(void **)&c->d_framek, (size_t)q * ny * I4}, {(void **)&c->d_mks, (size_t)q * I4},
@@ -242,6 +248,9 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
     if (e == cudaSuccess) e = configure_kernels_tc(optin);
     if (e == cudaSuccess) e = configure_kernels_zh(optin);
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twy, ny, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twx, c->nx, c->stream);
     if (e == cudaSuccess) e = launch_twiddles(c->d_twq, q, c->stream);
@@ -1257,7 +1266,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale", "k_zb", "k_uhz"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale", "k_zb"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -1366,10 +1375,10 @@ extern "C" lrccs_status lrccs_get_plan(lrccs_ctx *c, lrccs_plan *plan) {
 }
 
 // The solver state one iteration reads and writes: U_t, U_{t-1}, B, the
-// scalars (step size, its schedule counter, SD) and the k_gdqr totals (the
-// right-hand sides U^H Z are formed from U_t at every B-step).
+// scalars (step size, its schedule counter, SD), the k_gdqr totals and its
+// partial sums of the next right-hand sides U^H Z.
 struct solver_state {
-    std::vector<float2> U, Up, B;
+    std::vector<float2> U, Up, B, hpart;
     std::vector<double> scal;
     std::vector<double2> tot;
     int t;
@@ -1381,7 +1390,9 @@ static lrccs_status save_state(lrccs_ctx *c, solver_state &s, size_t tot_len) {
     s.B.resize((size_t)c->q * c->r);
     s.scal.resize(SC_COUNT);
     s.tot.resize(tot_len);
+    s.hpart.resize((size_t)c->gd_grid * c->q * c->r);
     CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(s.hpart.data(), c->d_hpart, s.hpart.size() * sizeof(float2), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(s.U.data(), c->d_U, nu * sizeof(float2), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(s.Up.data(), c->d_Uprev, nu * sizeof(float2), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(s.B.data(), c->d_B, s.B.size() * sizeof(float2), cudaMemcpyDeviceToHost));
@@ -1397,6 +1408,7 @@ static lrccs_status restore_state(lrccs_ctx *c, const solver_state &s) {
     CK(cudaMemcpy(c->d_B, s.B.data(), s.B.size() * sizeof(float2), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_scal, s.scal.data(), SC_COUNT * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_tot, s.tot.data(), s.tot.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_hpart, s.hpart.data(), s.hpart.size() * sizeof(float2), cudaMemcpyHostToDevice));
     CK(cudaMemset(c->d_status, 0, sizeof(unsigned)));
     c->t = s.t;
     return LRCCS_OK;
@@ -1646,7 +1658,9 @@ extern "C" lrccs_status lrccs_forward_transform(lrccs_ctx *c, void *d_T, size_t 
 
 extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *out) {
     if (!c) return LRCCS_E_INVALID;
-    const int G = c->gd_grid, NTS = 9;   // the stamps of k_gdqr (GD_NTS)
+    // the stamps of k_gdqr per block: 9 clock64() points, then the global
+    // timer (ns) at entry and exit
+    const int G = c->gd_grid, NTS = 11, NCLK = 9;
     if (out) {
         if (!c->d_gdts) {
             set_err(c, "lrccs_gdqr_phases: phase timing is off");
@@ -1655,7 +1669,7 @@ extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *
         std::vector<long long> h((size_t)G * NTS);
         CK(cudaStreamSynchronize(c->stream));
         CK(cudaMemcpy(h.data(), c->d_gdts, h.size() * sizeof(long long), cudaMemcpyDeviceToHost));
-        for (int i = 0; i + 1 < NTS; ++i) {
+        for (int i = 0; i + 1 < NCLK; ++i) {
             double sum = 0.0, mx = 0.0;
             for (int b = 0; b < G; ++b) {
                 const double d = (double)(h[(size_t)b * NTS + i + 1] - h[(size_t)b * NTS + i]);
@@ -1665,11 +1679,22 @@ extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *
             out[2 * i] = sum / G;
             out[2 * i + 1] = mx;
         }
+        long long e0 = h[NCLK], e1 = h[NCLK], x1 = h[NCLK + 1];
+        for (int b = 0; b < G; ++b) {
+            const long long e = h[(size_t)b * NTS + NCLK], x = h[(size_t)b * NTS + NCLK + 1];
+            e0 = e < e0 ? e : e0;
+            e1 = e > e1 ? e : e1;
+            x1 = x > x1 ? x : x1;
+        }
+        out[2 * (NCLK - 1)] = (double)(x1 - e0);       // first entry to last exit (ns)
+        out[2 * (NCLK - 1) + 1] = (double)(e1 - e0);   // spread of the blocks' entries (ns)
     }
     if (enable && !c->d_gdts) {
         if (!dalloc(c, &c->d_gdts, (size_t)G * NTS)) return LRCCS_E_NOMEM;
         CK(cudaMemset(c->d_gdts, 0, (size_t)G * NTS * sizeof(long long)));
+        drop_iter_graph(c);   // captured iterations take the stamps from now on
     } else if (!enable && c->d_gdts && !out) {
+        drop_iter_graph(c);
         cudaFree(c->d_gdts);
         c->d_gdts = nullptr;
     }

@@ -50,8 +50,8 @@ enum {
     KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT,
     // precision forms of the forward transform (tcgen05 GEMM)
     KID_TC_A, KID_TC_GEMM, KID_TC_SCALE,
-    // the contractions with Z (Z B^H for the gradient, U^H Z for the B-step)
-    KID_ZB, KID_UHZ, KID_COUNT
+    // Z B^H of the gradient
+    KID_ZB, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -156,7 +156,9 @@ struct lrccs_ctx {
     float2 *d_Q;                 // q * q rotations of the eigensolver's refine pass
     double2 *d_tot;              // k_gdqr totals: [grad^H grad | U^H grad | U^H U] (iteration), [U+^H U+] (init)
     float2 *d_ZB;                // n * rmax  Z B^H (k_zb)
-    float2 *d_hpart;             // uhz_grid_of(n) * q * rmax  per-block partial sums of U^H Z (k_uhz)
+    float2 *d_hpart;             // gd_grid * q * rmax  per-block partial sums of h = U^H Z (k_gdqr)
+    cudaStream_t side;           // parallel branch of the iteration (k_zb beside the adjoint passes)
+    cudaEvent_t ev_fork, ev_join;
 
     // general (2D) masks: the union Omega_u of the frames' samples, kept row by
     // row (points of row ky at u in [uptr[ky], uptr[ky+1]), ascending kx)
@@ -236,8 +238,6 @@ cudaError_t launch_gram_x0(lrccs_ctx *c);
 cudaError_t launch_u0(lrccs_ctx *c);
 cudaError_t launch_gdqr(lrccs_ctx *c, int mode);      // F: GD step + Cholesky QR (mode 0: init U+)
 cudaError_t launch_zb(lrccs_ctx *c);                  // d_ZB <- Z B^H
-cudaError_t launch_uhz(lrccs_ctx *c);                 // d_hpart <- partial sums of U^H Z
-int uhz_grid_of(int n);                               // blocks (partial-sum rows) of k_uhz
 cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);

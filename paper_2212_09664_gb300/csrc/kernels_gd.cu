@@ -9,21 +9,23 @@
 //                = U^H U - eta (U^H grad + grad^H U) + eta^2 grad^H grad,
 //            G1 = R1^H R1 (Cholesky), R1^{-1}
 //   phase 2  U_{t+1} = (U - eta grad) R1^{-1}  (the QR step of Alg. 2 as
-//            Cholesky QR), pixel by pixel; the last block out forms
-//            SD(U_t, U_{t+1}) from U_t^H U_{t+1} = (U^H U - eta U^H grad) R1^{-1}.
+//            Cholesky QR), and per block the partial sums of the next
+//            B-step's right-hand sides h = U_{t+1}^H Z (the solve adds the
+//            blocks' rows in order); the last block out forms SD(U_t, U_{t+1})
+//            from U_t^H U_{t+1} = (U^H U - eta U^H grad) R1^{-1}.
 //
 // G1 is formed from the exact U^H U of the current (FP32) iterate, so each
 // iteration removes the loss of orthogonality of the previous one; with
 // ||eta grad|| <= eta_c-sized steps G1 is well conditioned and one Cholesky
 // QR pass leaves U_{t+1} orthonormal to FP32 rounding.
 //
-// In init mode the same kernel orthonormalises the given U+ (G1 = U+^H U+).
+// In init mode the same kernel orthonormalises the given U+ (G1 = U+^H U+)
+// and forms the first right-hand sides U_0^H Z.
 // A block's pixel range stays in shared memory across the phases when it
 // fits; otherwise each phase re-stages it in chunks.
 //
-// The two contractions with Z = [A_k^H y_k] run as their own pixel-parallel
-// kernels: k_zb (Z B^H, after the B-step) and k_uhz (the B-step's right-hand
-// sides U^H Z, partial sums per block, added up by the solve).
+// Z B^H depends only on the B-step's result, so its own kernel k_zb forms it
+// while the adjoint transforms run (a parallel branch of the iteration).
 //
 // Partial sums are FP32 within a block and FP64 across blocks, reduced in a
 // fixed order (deterministic).  The grid barriers spin on a global counter
@@ -40,6 +42,8 @@
 struct GdArgs {
     const float2 *Gk;   // n x r   sum_j conj(d_j) F^H K_j (iteration mode)
     const float2 *ZB;   // n x r   Z B^H (iteration mode)
+    const float2 *Z;    // n x q   A_k^H y_k, row-major (i q + k)
+    float2 *hpart;      // G x q r partial sums of h = U_{t+1}^H Z (row b: block b)
     float2 *U;          // n x r   U_t in, U_{t+1} out
     float2 *Uprev;      // n x r   receives U_t (iteration mode)
     const float2 *Up;   // n x r   U+ (init mode)
@@ -49,7 +53,7 @@ struct GdArgs {
     double *scal;       // SC_* scalars
     unsigned int *bar;  // [0] barrier arrivals, [1] exit count
     unsigned int *status;
-    int n, r, chunk, resident, mode;
+    int n, r, q, zs, chunk, resident, mode;
     double eta_c;
     double eta_scale0, eta_decay;   // variable step size: eta_t = eta eta_scale0 eta_decay^k
     long long *ts;             // NULL, or GD_NTS clock64() stamps per block (phase timing)
@@ -58,11 +62,20 @@ struct GdArgs {
 };
 
 // Phase timing (measurement support): thread 0 of every block stamps clock64()
-// at GD_NTS points of the kernel when a.ts is set.
-#define GD_NTS 9
+// at 9 points of the kernel, and the global timer (ns) at its entry and exit,
+// when a.ts is set.
+#define GD_NTS 11
 #define GD_TS(i)                                                                    \
     do {                                                                            \
         if (a.ts && threadIdx.x == 0) a.ts[(size_t)blockIdx.x * GD_NTS + (i)] = clock64(); \
+    } while (0)
+#define GD_GT(i)                                                                    \
+    do {                                                                            \
+        if (a.ts && threadIdx.x == 0) {                                             \
+            unsigned long long g_;                                                  \
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g_));                  \
+            a.ts[(size_t)blockIdx.x * GD_NTS + (i)] = (long long)g_;                \
+        }                                                                           \
     } while (0)
 
 // ---------------------------------------------------------------- grid-wide steps
@@ -247,12 +260,14 @@ static __device__ void tiles_write(const float2 (&acc)[2][4], int T, int S, floa
 
 template <int R>
 __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
+    GD_GT(9);
     extern __shared__ __align__(16) float2 smem[];
     constexpr int r = R;
-    const int chunk = a.chunk;
+    const int q = a.q, zs = a.zs, chunk = a.chunk;
     float2 *s_u = smem;                 // chunk * r : U_t (iteration) or U+ (init)
     float2 *s_a = s_u + chunk * r;      // chunk * r : Gk, grad, then U_{t+1}
     float2 *s_w = s_a + chunk * r;      // chunk * r : Z B^H, then U - eta grad
+    float2 *s_z = s_w + chunk * r;      // chunk * zs: Z (for h = U_{t+1}^H Z)
     __shared__ float2 sL[R * R];
     __shared__ float2 sR[R * R];
     __shared__ float sinv[R];
@@ -326,7 +341,13 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
         }
         cp_async_commit();
-        cp_async_wait();
+        if (a.resident) {   // Z for phase 2 streams in behind phase 1
+            stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
+            cp_async_commit();
+            cp_async_wait_1();
+        } else {
+            cp_async_wait();
+        }
         __syncthreads();
         if (c0 == i0) GD_TS(1);
         if (iter) {   // grad = Gk - Z B^H
@@ -433,6 +454,15 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
     const float etaf = iter ? s_eta : 0.f;
 
     // ------------------------------------------------ phase 2: U_{t+1} = (U - eta grad) R1^{-1}
+    // and the partial sums of h = U_{t+1}^H Z over the block's pixels, thread
+    // (frame pair kp, slice hs) holding all R columns for frames 2 kp, 2 kp + 1
+    const int tq = (q + 1) >> 1;
+    const int Sh = max(1, NTG / tq), Hth = tq * Sh;
+    const bool hthr = t < Hth;
+    const int hk = 2 * (t % tq), hs = t / tq;
+    float2 pv[2 * R];
+#pragma unroll
+    for (int v = 0; v < 2 * R; ++v) pv[v] = make_float2(0.f, 0.f);
     for (int c0 = i0; c0 < i1; c0 += chunk) {
         const int cn = min(chunk, i1 - c0);
         if (!a.resident) {
@@ -443,9 +473,10 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             } else {
                 stage_rows(s_u, r, a.Up + (size_t)c0 * r, r, cn, r);
             }
+            stage_rows(s_z, zs, a.Z + (size_t)c0 * q, q, cn, q);
             cp_async_commit();
-            cp_async_wait();
         }
+        cp_async_wait();
         __syncthreads();
         for (int e = t; e < cn * r; e += NTG) s_w[e] = iter ? csub(s_u[e], cscale(s_a[e], etaf)) : s_u[e];
         __syncthreads();
@@ -455,15 +486,57 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
 #pragma unroll
             for (int m = 0; m < R; ++m)
                 if (m <= l) cfma(v, s_w[ii * r + m], sR[m * r + l]);
+            s_a[e] = v;
             a.U[(size_t)c0 * r + e] = v;
             if (iter) a.Uprev[(size_t)c0 * r + e] = s_u[e];
+        }
+        __syncthreads();
+        if (hthr) {
+#pragma unroll(R <= 12 ? 2 : 1)
+            for (int ii = hs; ii < cn; ii += Sh) {
+                const float4 z = *(const float4 *)(s_z + ii * zs + hk);   // Z[k], Z[k+1] (pad column when k+1 = q)
+                const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
+#pragma unroll
+                for (int l = 0; l < R; ++l) {
+                    const float2 u = s_a[ii * r + l];
+                    cfmac(pv[l], u, z0);
+                    cfmac(pv[R + l], u, z1);
+                }
+            }
+        }
+    }
+    // the block's row of h partial sums, hpart[b][k r + l], slices added in
+    // order, V values per thread per round (s_w and s_z are free now)
+    {
+        const int cap2 = chunk * (r + zs);
+        float2 *scr = cap2 >= 2 * NTG ? s_w : s_red2;
+        const int V = max(2, min(2 * R, ((cap2 >= 2 * NTG ? cap2 : 2 * NTG) / NTG) & ~1));
+        float2 *hrow = a.hpart + (size_t)blockIdx.x * q * r;
+        for (int v0 = 0; v0 < 2 * R; v0 += V) {
+            __syncthreads();
+            if (hthr) {
+#pragma unroll
+                for (int v = 0; v < 2 * R; ++v)
+                    if (v >= v0 && v < v0 + V) scr[(v - v0) * NTG + t] = pv[v];
+            }
+            __syncthreads();
+            const int vn = min(V, 2 * R - v0);
+            for (int w = t; w < vn * tq; w += NTG) {
+                const int dv = w / tq, kp = w - dv * tq, v = v0 + dv;
+                const int k = 2 * kp + v / R, l = v % R;
+                if (k < q) {
+                    float2 sum = make_float2(0.f, 0.f);
+                    for (int ss = 0; ss < Sh; ++ss) sum = cadd(sum, scr[dv * NTG + ss * tq + kp]);
+                    hrow[k * r + l] = sum;
+                }
+            }
         }
     }
     GD_TS(8);
     // the last block out: SD(U_t, U_{t+1})^2 = r - ||U_t^H U_{t+1}||_F^2 with
-    // U_t^H U_{t+1} = (U_t^H U_t - eta U_t^H grad) R1^{-1} from the FP64 totals
-    // (no second reduction), and the barrier counters back to zero (every block
-    // is past its last barrier)
+    // U_t^H U_{t+1} = (U_t^H U_t - eta U_t^H grad) R1^{-1} from the totals (no
+    // second reduction; thread x r + y forms entry (x, y)), and the barrier
+    // counters back to zero (every block is past its last barrier)
     __syncthreads();
     if (t == 0) {
         __threadfence();
@@ -471,27 +544,31 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         s_flag = prev == (unsigned)G - 1;
     }
     __syncthreads();
-    if (!s_flag) return;
-    if (t < 32) {
-        double sum = 0.0;
-        if (iter) {
-            const double etad = (double)etaf;
-            for (int e = t; e < rr; e += 32) {
-                const int x = e / r, y = e - x * r;
-                double mr = 0.0, mi = 0.0;
-                for (int m = 0; m <= y; ++m) {
-                    const int p = x <= m ? pair_index(x, m, r) : pair_index(m, x, r);
-                    const double2 uu = __ldcg(a.tot + np + rr + p);
-                    const double2 ug = __ldcg(a.tot + np + x * r + m);
-                    const double cr = uu.x - etad * ug.x;
-                    const double ci = (x <= m ? uu.y : -uu.y) - etad * ug.y;
-                    const float2 q = sR[m * r + y];
-                    mr += cr * (double)q.x - ci * (double)q.y;
-                    mi += cr * (double)q.y + ci * (double)q.x;
-                }
-                sum += mr * mr + mi * mi;
+    if (!s_flag) {
+        GD_GT(10);
+        return;
+    }
+    double sq = 0.0;
+    if (iter && t < rr) {
+        const float2 *A2 = s_tot + np, *A3 = s_tot + np + rr;
+        const int x = t / r, y = t - x * r;
+        float2 mv = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            if (m <= y) {
+                const float2 uu = x <= m ? A3[pair_index(x, m, r)] : cconj(A3[pair_index(m, x, r)]);
+                cfma(mv, csub(uu, cscale(A2[x * r + m], etaf)), sR[m * r + y]);
             }
         }
+        sq = (double)mv.x * mv.x + (double)mv.y * mv.y;
+    }
+    // block sum in a fixed order: warps, then warp 0 over the warp sums
+    __shared__ double s_sq[NTG / 32];
+    sq = warp_sum_d(sq);
+    if ((t & 31) == 0) s_sq[t >> 5] = sq;
+    __syncthreads();
+    if (t < 32) {
+        double sum = t < NTG / 32 ? s_sq[t] : 0.0;
         sum = warp_sum_d(sum);
         if (t == 0) {
             if (iter) {
@@ -502,6 +579,7 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             a.bar[1] = 0u;
         }
     }
+    GD_GT(10);
 }
 
 // ---------------------------------------------------------------- Z contractions
@@ -547,75 +625,6 @@ __global__ void __launch_bounds__(256) k_zb(const float2 *__restrict__ Z, const 
         if (j < nl) ZB[(size_t)(i0 + p) * R + l0 + j] = acc[j];
 }
 
-// Partial sums of h = U^H Z (r x q, the B-step's right-hand sides h_k =
-// (A_k U)^H y_k = U^H Z[:, k], Alg. 2) over the block's UH_PIX pixels:
-// hpart[b][k r + l] = sum_i conj(U[i][l]) Z[i][k].  Thread = (pair of frames,
-// slice of the pixels); the slices are added in a fixed order.  The per-frame
-// totals are formed by the B-step's solve, which adds the blocks' rows in order.
-#define UH_PIX 128
-template <int R>
-__global__ void __launch_bounds__(256) k_uhz(const float2 *__restrict__ U, const float2 *__restrict__ Z, int n, int q,
-                                             float2 *__restrict__ hpart) {
-    extern __shared__ __align__(16) float2 smem[];
-    const int zs = ((q + 1) | 3) - 1;   // even, 2 mod 4: 16-byte loads of consecutive frame pairs
-    float2 *s_z = smem;                 // UH_PIX * zs
-    float2 *s_u = s_z + UH_PIX * zs;    // UH_PIX * R
-    const int i0 = blockIdx.x * UH_PIX, cn = min(UH_PIX, n - i0);
-    const int t = threadIdx.x;
-    if ((q & 1) == 0) {
-        const int h = q >> 1;
-        for (int e = t; e < cn * h; e += blockDim.x) {
-            const int ii = e / h, c2 = e - ii * h;
-            cp_async16(s_z + ii * zs + 2 * c2, Z + (size_t)(i0 + ii) * q + 2 * c2);
-        }
-    } else {
-        for (int e = t; e < cn * q; e += blockDim.x) {
-            const int ii = e / q, k = e - ii * q;
-            cp_async8(s_z + ii * zs + k, Z + (size_t)i0 * q + e);
-        }
-    }
-    for (int e = t; e < cn * R; e += blockDim.x) cp_async8(s_u + e, U + (size_t)i0 * R + e);
-    cp_async_commit();
-    cp_async_wait();
-    __syncthreads();
-    if (q & 1)   // the pad column read with the last frame pair
-        for (int ii = t; ii < cn; ii += blockDim.x) s_z[ii * zs + q] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const int tq = (q + 1) >> 1, S = max(1, (int)blockDim.x / tq);
-    const int kp = t % tq, s = t / tq, k = 2 * kp;
-    float2 pv[2 * R];
-#pragma unroll
-    for (int v = 0; v < 2 * R; ++v) pv[v] = make_float2(0.f, 0.f);
-    if (s < S) {
-#pragma unroll 2
-        for (int ii = s; ii < cn; ii += S) {
-            const float4 z = *(const float4 *)(s_z + ii * zs + k);
-            const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
-#pragma unroll
-            for (int l = 0; l < R; ++l) {
-                const float2 u = s_u[ii * R + l];
-                cfmac(pv[l], u, z0);
-                cfmac(pv[R + l], u, z1);
-            }
-        }
-    }
-    // slices in order: the staging area is free now (2 R values per thread)
-    __syncthreads();
-    float2 *scr = smem;   // 2 R blockDim.x <= UH_PIX (zs + R) for every q >= 1, R <= 16
-    if (s < S) {
-#pragma unroll
-        for (int v = 0; v < 2 * R; ++v) scr[v * blockDim.x + t] = pv[v];
-    }
-    __syncthreads();
-    for (int o = t; o < q * R; o += blockDim.x) {
-        const int kk = o / R, l = o - kk * R;
-        const int v = (kk & 1) * R + l, kpp = kk >> 1;
-        float2 sum = make_float2(0.f, 0.f);
-        for (int ss = 0; ss < S; ++ss) sum = cadd(sum, scr[v * blockDim.x + ss * tq + kpp]);
-        hpart[(size_t)blockIdx.x * q * R + o] = sum;
-    }
-}
-
 // ---------------------------------------------------------------- launcher
 
 typedef void (*gd_kernel_t)(GdArgs);
@@ -637,11 +646,16 @@ cudaError_t configure_kernels_gd(int max_smem) {
     return cudaSuccess;
 }
 
+// Z row stride in shared memory: q rounded up to 2 mod 4 complex values, so
+// that 16-byte loads of consecutive pixels' rows hit distinct banks.
+static int z_stride(int q) { return ((q + 1) | 3) - 1; }
+
 cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
-    const int r = c->r, G = c->gd_grid;
+    const int r = c->r, q = c->q, G = c->gd_grid;
     if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
+    const int zs = z_stride(q);
     const int per = (c->n + G - 1) / G;
-    const size_t bpp = (size_t)3 * r * sizeof(float2);
+    const size_t bpp = (size_t)(3 * r + zs) * sizeof(float2);
     const size_t avail = (size_t)(c->dev_smem_optin - g_gd_static_smem[r - 1]);
     int chunk = (int)(avail / bpp) & ~1;
     chunk = min(chunk, 512);
@@ -650,6 +664,8 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     GdArgs a;
     a.Gk = c->d_Up;
     a.ZB = c->d_ZB;
+    a.Z = c->d_Z;
+    a.hpart = c->d_hpart;
     a.U = c->d_U;
     a.Uprev = c->d_Uprev;
     a.Up = c->d_Up;
@@ -661,6 +677,8 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.status = c->d_status;
     a.n = c->n;
     a.r = r;
+    a.q = q;
+    a.zs = zs;
     a.chunk = chunk;
     a.resident = chunk >= per ? 1 : 0;
     a.mode = mode;
@@ -669,7 +687,7 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
     a.eta_decay = c->prm.eta_decay > 0.0 ? c->prm.eta_decay : 1.0;
     a.spin_limit = 1u << 24;
     a.bar_skew = 0;
-    a.ts = (mode == 1 && !c->capturing) ? c->d_gdts : nullptr;
+    a.ts = mode == 1 ? c->d_gdts : nullptr;   // also in captured iterations (phase timing on)
     if (c->test_timeout && !c->capturing) {   // lrccs_test_wait_timeout: this launch only
         a.spin_limit = 1u << 16;
         a.bar_skew = 1;
@@ -686,15 +704,8 @@ cudaError_t launch_gdqr(lrccs_ctx *c, int mode) {
 typedef void (*zb_kernel_t)(const float2 *, const float2 *, int, int, float2 *);
 #define RANK_TABLE(K) {K<1>, K<2>, K<3>, K<4>, K<5>, K<6>, K<7>, K<8>, K<9>, K<10>, K<11>, K<12>, K<13>, K<14>, K<15>, K<16>}
 static const zb_kernel_t kZb[RMAXC] = RANK_TABLE(k_zb);
-static const zb_kernel_t kUhz[RMAXC] = RANK_TABLE(k_uhz);
 
 static size_t zb_smem(int q, int r) { return ((size_t)ZB_PIX * (q | 1) + (size_t)q * r) * sizeof(float2); }
-static size_t uhz_smem(int q, int r) {
-    const size_t stage = (size_t)UH_PIX * ((((q + 1) | 3) - 1) + r), scr = (size_t)2 * r * 256;
-    return (stage > scr ? stage : scr) * sizeof(float2);
-}
-int uhz_grid_of(int n) { return (n + UH_PIX - 1) / UH_PIX; }
-
 // d_ZB <- Z B^H (the data term of the next gradient), from the current B.
 cudaError_t launch_zb(lrccs_ctx *c) {
     const int r = c->r;
@@ -706,25 +717,12 @@ cudaError_t launch_zb(lrccs_ctx *c) {
     return cudaGetLastError();
 }
 
-// d_hpart <- per-block partial sums of U^H Z at the current U (the B-step's
-// right-hand sides; the solve adds the uhz_grid_of(n) rows per frame).
-cudaError_t launch_uhz(lrccs_ctx *c) {
-    const int r = c->r;
-    if (r < 1 || r > RMAXC) return cudaErrorInvalidValue;
-    prof_begin(c, KID_UHZ);
-    kUhz[r - 1]<<<uhz_grid_of(c->n), 256, uhz_smem(c->q, r), c->stream>>>(c->d_U, c->d_Z, c->n, c->q, c->d_hpart);
-    prof_end(c, KID_UHZ);
-    return cudaGetLastError();
-}
-
 cudaError_t configure_kernels_zh(int max_smem) {
     for (int i = 0; i < RMAXC; ++i) {
         const int r = i + 1;
-        const size_t a = zb_smem(128, r), b = uhz_smem(128, r);   // the largest q
-        if ((int)a > max_smem || (int)b > max_smem) return cudaErrorInvalidConfiguration;
+        const size_t a = zb_smem(128, r);   // the largest q
+        if ((int)a > max_smem) return cudaErrorInvalidConfiguration;
         cudaError_t e = cudaFuncSetAttribute(kZb[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(kUhz[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -190,36 +190,41 @@ cudaError_t launch_compact_general(lrccs_ctx *c, const uint8_t *d_mask) {
 // few samples at the tile's columns (T[ky][x] = sum_s y_s e^{+2 pi i kx_s x / nx}
 // / sqrt(nx), plain and truncated), then the column tile is transformed back
 // along ky and multiplied by conj(d_j) into the coil sum.  Nothing the size of
-// full k-space rows goes through memory.
+// full k-space rows goes through memory.  The block's twiddles
+// e^{+2 pi i kx x / nx} (every kx, the tile's x) are tabulated once in shared
+// memory; a thread evaluates four columns of one row per pass over its samples.
 #define TXG 16
-#define IG_STAGE 4096   // samples of one coil staged at a time (a row has at most nx <= 256)
+#define IG_STAGE 512    // samples of one coil staged at a time (>= nx: a row always fits)
 template <int P>
-__global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, const int32_t *__restrict__ idx,
-                                                  const int32_t *__restrict__ framerows,
-                                                  const int32_t *__restrict__ lineptr,
-                                                  const int32_t *__restrict__ rowoff, const int32_t *__restrict__ rowcnt,
-                                                  const int32_t *__restrict__ fpk, const int32_t *__restrict__ mks,
-                                                  const float2 *__restrict__ smaps, const double *__restrict__ scal,
-                                                  const uint8_t *__restrict__ tflag, float2 *__restrict__ Z,
-                                                  float2 *__restrict__ X0, int nx, int q, int nc,
-                                                  const float2 *__restrict__ g_twy, const float2 *__restrict__ g_twx,
-                                                  float sy, float sx, float inv_nx) {
+__global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ y, const int32_t *__restrict__ idx,
+                                                     const int32_t *__restrict__ framerows,
+                                                     const int32_t *__restrict__ lineptr,
+                                                     const int32_t *__restrict__ rowoff,
+                                                     const int32_t *__restrict__ rowcnt,
+                                                     const int32_t *__restrict__ fpk, const int32_t *__restrict__ mks,
+                                                     const float2 *__restrict__ smaps, const double *__restrict__ scal,
+                                                     const uint8_t *__restrict__ tflag, float2 *__restrict__ Z,
+                                                     float2 *__restrict__ X0, int nx, int q, int nc,
+                                                     const float2 *__restrict__ g_twy, const float2 *__restrict__ g_twx,
+                                                     float sy, float sx) {
     constexpr int NY = 32 * P;
     constexpr int TP = 2 * TXG + 1;
     constexpr int ACC = (NY * 2 * TXG + 255) / 256;
     extern __shared__ __align__(16) float2 smem[];
     float2 *tile = smem;                  // NY * TP
-    float2 *s_S = tile + NY * TP;         // NY * TXG
-    float2 *s_twy = s_S + NY * TXG;       // NY
-    float2 *s_twx = s_twy + NY;           // nx
-    float2 *s_y = s_twx + 256;            // IG_STAGE staged samples of one coil
+    float2 *s_tw = tile + NY * TP;        // nx * TXG: e^{+2 pi i kx (x0 + xx) / nx} at kx * TXG + xx
+    float2 *s_twy = s_tw + nx * TXG;      // NY
+    float2 *s_y = s_twy + NY;             // IG_STAGE staged samples of one coil
     int16_t *s_kx = (int16_t *)(s_y + IG_STAGE);
     uint8_t *s_tr = (uint8_t *)(s_kx + IG_STAGE);
     __shared__ int s_grp[3];
     const int k = blockIdx.y, x0 = blockIdx.x * TXG;
     const int n = NY * nx;
     load_twiddles(s_twy, g_twy, NY);
-    for (int t = threadIdx.x; t < nx; t += blockDim.x) s_twx[t] = g_twx[t];
+    for (int e = threadIdx.x; e < nx * TXG; e += blockDim.x) {
+        const int kx = e / TXG, xx = e - kx * TXG;
+        s_tw[e] = cconj(g_twx[(kx * (x0 + xx)) % nx]);
+    }
     const int lp = lineptr[k], L = lineptr[k + 1] - lp;
     const int f0 = fpk[k], mk = mks[k];
     float2 acc[ACC];
@@ -228,8 +233,6 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
     for (int j = 0; j < nc; ++j) {
         __syncthreads();
         for (int e = threadIdx.x; e < NY * TP; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
-        for (int e = threadIdx.x; e < NY * TXG; e += blockDim.x)
-            s_S[e] = smaps[(size_t)j * n + (size_t)(e / TXG) * nx + x0 + (e % TXG)];
         const int64_t yb = (int64_t)nc * f0 + (int64_t)j * mk;   // sample f0 + s of coil j at y[yb + s]
         // the frame's rows in groups whose samples fit the staging area
         for (int g0 = 0; g0 < L;) {
@@ -248,34 +251,41 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
             }
             __syncthreads();
             const int g1 = s_grp[0], sbase = s_grp[1], scnt = s_grp[2];
-            // stage the group's samples of coil j: value (zeroed in the truncated
-            // copy when |y|^2 > gamma) and kx
+            // stage the group's samples of coil j: value, kx, and the truncation
+            // flag (1: |y|^2 > gamma, dropped from the truncated copy)
             for (int e = threadIdx.x; e < scnt; e += blockDim.x) {
                 const int s = sbase + e;
-                const float2 a = __ldg(y + yb + (s - f0));
-                s_y[e] = a;
+                s_y[e] = __ldg(y + yb + (s - f0));
                 s_kx[e] = (int16_t)(__ldg(idx + s) % nx);
                 s_tr[e] = tflag[yb + (s - f0)];
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < (g1 - g0) * TXG; e += blockDim.x) {
-                const int li = g0 + e / TXG, xx = e % TXG, x = x0 + xx;
+            // item (row li, column quad cq): columns x0 + 4 cq .. x0 + 4 cq + 3
+            for (int e = threadIdx.x; e < (g1 - g0) * (TXG / 4); e += blockDim.x) {
+                const int li = g0 + e / (TXG / 4), cq = e % (TXG / 4);
                 const int ky = framerows[lp + li];
                 const int off = rowoff[k * NY + ky] - sbase, cnt = rowcnt[k * NY + ky];
-                float2 vp = make_float2(0.f, 0.f), vt = make_float2(0.f, 0.f);
+                float2 vp[4], vt[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) vp[jj] = vt[jj] = make_float2(0.f, 0.f);
                 for (int s = off; s < off + cnt; ++s) {
                     const float2 a = s_y[s];
-                    // (kx x) mod nx without an integer division: kx x < 2^16 is exact in FP32
-                    const int p = (int)s_kx[s] * x;
-                    int m = p - nx * (int)((float)p * inv_nx);
-                    m += m < 0 ? nx : 0;
-                    m -= m >= nx ? nx : 0;
-                    const float2 w = cconj(s_twx[m]);   // e^{+2 pi i kx x / nx}
-                    cfma(vp, a, w);
-                    if (!s_tr[s]) cfma(vt, a, w);   // kept by the truncation (|y|^2 <= gamma)
+                    const float4 *w4 = (const float4 *)(s_tw + (int)s_kx[s] * TXG + 4 * cq);
+                    const float4 wa = w4[0], wb = w4[1];
+                    const float2 w[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                         make_float2(wb.z, wb.w)};
+                    const bool keep = s_tr[s] == 0;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        cfma(vp[jj], a, w[jj]);
+                        if (keep) cfma(vt[jj], a, w[jj]);
+                    }
                 }
-                tile[ky * TP + 2 * xx] = cscale(vp, sx);
-                tile[ky * TP + 2 * xx + 1] = cscale(vt, sx);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    tile[ky * TP + 2 * (4 * cq + jj)] = cscale(vp[jj], sx);
+                    tile[ky * TP + 2 * (4 * cq + jj) + 1] = cscale(vt[jj], sx);
+                }
             }
             g0 = g1;
         }
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(256) k_init_gen(const float2 *__restrict__ y, 
             const int e = threadIdx.x + 256 * u;
             if (e < NY * 2 * TXG) {
                 const int yy = e / (2 * TXG), cc = e % (2 * TXG);
-                cfmac(acc[u], s_S[yy * TXG + (cc >> 1)], tile[yy * TP + cc]);
+                cfmac(acc[u], __ldg(smaps + (size_t)j * n + (size_t)yy * nx + x0 + (cc >> 1)), tile[yy * TP + cc]);
             }
         }
     }
@@ -315,7 +325,7 @@ __global__ void k_trunc_flags(const float2 *__restrict__ y, int64_t count, const
 
 cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y) {
     const float sx = (float)(1.0 / sqrt((double)c->nx)), sy = (float)(1.0 / sqrt((double)c->ny));
-    const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->ny * TXG + c->ny + 256 + IG_STAGE) * sizeof(float2) +
+    const size_t smem = ((size_t)c->ny * (2 * TXG + 1) + (size_t)c->nx * TXG + c->ny + IG_STAGE) * sizeof(float2) +
                         (size_t)IG_STAGE * (sizeof(int16_t) + 1);
     prof_begin(c, KID_INIT_GEN);
     k_trunc_flags<<<4 * 152, 256, 0, c->stream>>>(d_y, (int64_t)c->nc * c->total, c->d_scal, c->d_tflag);
@@ -326,7 +336,7 @@ cudaError_t launch_init_general(lrccs_ctx *c, const float2 *d_y) {
         k_init_gen<P_><<<grid, 256, smem, c->stream>>>(d_y, c->d_idx, c->d_framerows, c->d_lineptr, c->d_rowoff,
                                                        c->d_rowcnt, c->d_fpk, c->d_mks, c->d_smaps, c->d_scal,
                                                        c->d_tflag, c->d_Z, c->d_X0, c->nx, c->q, c->nc, c->d_twy,
-                                                       c->d_twx, sy, sx, (float)(1.0 / (double)c->nx));
+                                                       c->d_twx, sy, sx);
         prof_end(c, KID_INIT_GEN);
     });
     return cudaGetLastError();

@@ -13,16 +13,15 @@
 // and by Parseval the row Gram FU^H FU of a row equals T^H T of the same row:
 // one iteration needs only the C r column transforms F_y and F_y^H.
 //
-// Kernels (one launch each per iteration; C is in kernels_solve.cu, H, I and F in kernels_gd.cu):
-//   H k_uhz       : partial sums of h = U^H Z per pixel block       -> hpart
+// Kernels (one launch each per iteration; C is in kernels_solve.cu, I and F in kernels_gd.cu):
 //   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l] (sampled rows)
 //   B k_row_gram  : coil-summed row Gram sum_j T_j^H T_j per sampled row -> P[ky] (clusters)
-//   C k_solve     : G_k = sum of its rows' P, h_k (sum of hpart), Cholesky -> B
-//   I k_zb        : Z B^H                                           -> ZB
+//   C k_solve     : G_k = sum of its rows' P, h_k (sum of k_gdqr's partial rows), Cholesky -> B
+//   I k_zb        : Z B^H, on a parallel branch beside D and E          -> ZB
 //   D k_row_w     : T_j[ky, :] <- T_j[ky, :] W_ky                    -> T (in place)
 //   E k_adj_cols  : F_y^H, conj(d_j) coil sum                      -> Gk
 //   F k_gdqr      : grad = Gk - Z B^H, eta (t = 1), U - eta grad and its
-//                   Cholesky QR, SD                                  (kernels_gd.cu)
+//                   Cholesky QR, partial sums of the next h = U^H Z, SD (kernels_gd.cu)
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
 #include <cooperative_groups.h>
@@ -468,16 +467,29 @@ static cudaError_t launch_fwd_cols(lrccs_ctx *c) {
 // the iteration's coil-summed inverse transform goes to the U+ buffer (free during iterations)
 static cudaError_t launch_adj_cols(lrccs_ctx *c) { return launch_adj_cols_to(c, c->d_Up, c->r); }
 
+// Z B^H on the context's side stream, forked from (and later joined back
+// into) its stream: a parallel branch when the iteration is captured.
+static cudaError_t fork_zb(lrccs_ctx *c) {
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    cudaStream_t main_stream = c->stream;
+    c->stream = c->side;
+    e = launch_zb(c);
+    c->stream = main_stream;
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    return e;
+}
+static cudaError_t join_zb(lrccs_ctx *c) { return cudaStreamWaitEvent(c->stream, c->ev_join, 0); }
+
 cudaError_t launch_iteration(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
-    cudaError_t el = launch_uhz(c);        // the B-step's right-hand sides U^H Z
-    if (el != cudaSuccess) return el;
-    el = launch_fwd_cols(c);               // A
+    cudaError_t el = launch_fwd_cols(c);   // A
     if (el != cudaSuccess) return el;
     if (c->general) {                      // 2D masks: x transforms, per-point Grams and W (kernels_general.cu)
         el = launch_iteration_general_front(c);
         if (el != cudaSuccess) return el;
-        el = launch_zb(c);                 // Z B^H of the gradient
+        el = fork_zb(c);                   // I
         if (el != cudaSuccess) return el;
         el = launch_iteration_general_back(c);
         if (el != cudaSuccess) return el;
@@ -485,11 +497,13 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
         el = launch_row_gram(c);           // B
         if (el != cudaSuccess) return el;
         launch_solve(c);                   // C
-        el = launch_zb(c);                 // Z B^H of the gradient
+        el = fork_zb(c);                   // I
         if (el != cudaSuccess) return el;
         launch_row_w(c);                   // D
     }
     el = launch_adj_cols(c);               // E
+    if (el != cudaSuccess) return el;
+    el = join_zb(c);
     if (el != cudaSuccess) return el;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -506,13 +520,12 @@ cudaError_t launch_forward(lrccs_ctx *c) {
     return cudaGetLastError();
 }
 
-// The B-step alone at the current U: U^H Z, forward transforms, Grams and the
-// per-frame solves.
+// The B-step alone at the current U (the partial sums of U^H Z left by the
+// k_gdqr launch that formed U): forward transforms, Grams and the per-frame
+// solves.
 cudaError_t launch_bstep(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
-    cudaError_t el = launch_uhz(c);
-    if (el != cudaSuccess) return el;
-    el = launch_fwd_cols(c);
+    cudaError_t el = launch_fwd_cols(c);
     if (el != cudaSuccess) return el;
     if (c->general) return launch_iteration_general_front(c);
     el = launch_row_gram(c);

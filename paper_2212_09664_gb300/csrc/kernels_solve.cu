@@ -2,8 +2,8 @@
 // frame k the r x r least squares  G_k b_k = h_k  with
 //   G_k = (A_k U)^H (A_k U) = sum over the frame's sampled rows ky of the
 //         coil-summed row Grams P[ky] (k_row_gram),
-//   h_k = (A_k U)^H y_k = U^H Z[:, k] (the per-block partial sums of k_uhz,
-//         added here in block order),
+//   h_k = (A_k U)^H y_k = U^H Z[:, k] (the per-block partial sums left by
+//         k_gdqr, added here in block order),
 // solved by an FP32 Cholesky factorisation, one block per frame.
 #include <math.h>
 
@@ -13,7 +13,7 @@
 #define RMAXC 16   // compile-time bound on the rank
 #define NT 256     // threads per block
 
-// h_k = U^H Z[:, k] from the P partial rows of k_uhz (hpart[b][k r + l]):
+// h_k = U^H Z[:, k] from the P partial rows of k_gdqr (hpart[b][k r + l]):
 // thread (l, slice s) adds rows b = s, s + S, ... as compensated FP32 pairs,
 // then lane l of the first warp adds the slices in order.  Every thread of
 // the block calls it; lanes l < R of warp 0 return h_k[l].
@@ -147,13 +147,13 @@ cudaError_t launch_solve(lrccs_ctx *c) {
         kFrameGramGen[c->r - 1]<<<dim3(c->q, GEN_NCH), NT, 0, c->stream>>>(c->d_Pu, c->d_fpk, c->d_fu, c->d_fpart);
         prof_end(c, KID_SOLVE_GEN);
         prof_begin(c, KID_SOLVE_GEN);
-        kSolveGen[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_fpart, c->d_hpart, uhz_grid_of(c->n), c->q, c->d_fpk,
+        kSolveGen[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_fpart, c->d_hpart, c->gd_grid, c->q, c->d_fpk,
                                                         c->d_B, c->d_status);
         prof_end(c, KID_SOLVE_GEN);
         return cudaGetLastError();
     }
     prof_begin(c, KID_SOLVE);
-    kSolve[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_P, c->d_hpart, uhz_grid_of(c->n), c->q, c->d_lineptr,
+    kSolve[c->r - 1]<<<c->q, NT, 0, c->stream>>>(c->d_P, c->d_hpart, c->gd_grid, c->q, c->d_lineptr,
                                                  c->d_framerows, c->d_B, c->d_status);
     prof_end(c, KID_SOLVE);
     return cudaGetLastError();

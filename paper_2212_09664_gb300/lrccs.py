@@ -318,10 +318,12 @@ def lrccs_forward_transform(ctx, T):
 
 
 def lrccs_gdqr_phases(ctx, enable: bool = True, read: bool = False):
-    """Phase timing of the GD/QR kernel: returns [(mean, max) cycles] per interval when read."""
-    out = (C.c_double * 16)() if read else None
+    """Phase timing of the GD/QR kernel.  When read: [(mean, max) SM cycles] for
+    each of the 8 intervals, then (first entry to last exit, spread of the
+    entries) in ns."""
+    out = (C.c_double * 18)() if read else None
     _check(ctx, _lib.lrccs_gdqr_phases(ctx, 1 if enable else 0, out))
-    return [(out[2 * i], out[2 * i + 1]) for i in range(8)] if read else None
+    return [(out[2 * i], out[2 * i + 1]) for i in range(9)] if read else None
 
 
 def lrccs_test_wait_timeout(ctx, enable: bool = True):

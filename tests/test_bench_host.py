@@ -20,8 +20,8 @@ def test_algorithmic_bytes_of_the_cardiac_workload():
     assert kb["k_row_gram"] == 8 * 3409920                           # sampled rows in
     assert kb["k_row_w"] == 8 * 2 * 3409920                          # sampled rows in and out
     assert kb["k_adj_cols"] == 8 * (3409920 + 442368 + 368640)       # rows, maps in; n x r out
-    assert kb["k_gdqr"] == 8 * 6 * 368640 == 17694720               # Gk, U, Z B^H in; grad, U_t+1, U_t out
-    assert kb["k_zb"] == kb["k_uhz"] == 8 * (1769472 + 368640)       # Z and an n x r matrix
+    assert kb["k_gdqr"] == 8 * (6 * 368640 + 1769472) == 31850496   # Gk, U, Z B^H, Z in; grad, U_t+1, U_t out
+    assert kb["k_zb"] == 8 * (1769472 + 368640)                      # Z in, Z B^H out
     assert bench.iteration_bytes(p, 10, n_used) == sum(kb.values())
 
 
