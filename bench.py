@@ -936,6 +936,8 @@ def main():
                 dtype="f32", data="synthetic",
                 config=dict(workload=WORKLOAD, ny=p.ny, nx=p.nx, q=p.q, coils=p.nc, rank=p.rank,
                             iterations=T_ITER, sampled_rows=n_used, l2="flushed between timed steps (256 MB write)",
+                            coil_maps="trigonometric polynomials of <= 9 low-order modes with unit sum of squares "
+                                      "per pixel (stand-in for Gaussian bumps on a ring: same shapes and cost)",
                             parallelism="replicas" if ws > 1 else "single GPU"),
                 e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                 gpu_launches=launches, roofline=roof,

@@ -451,6 +451,40 @@ LRCCS_DEV void cp_async_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "me
 // wait until at most one committed group is still pending (double buffering)
 LRCCS_DEV void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// ---------------------------------------------------------------- tensor copies (TMA)
+// A 2D tile of a tensor map (cp.async.bulk.tensor) lands in shared memory and
+// completes a transaction count on an mbarrier: one thread arms the barrier
+// with the tile bytes and issues the copies, every thread waits on it.  The
+// wait is bounded: false when it gave up.
+
+LRCCS_DEV void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+LRCCS_DEV void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// tile at element coordinates (x, y) of the 2D map into dst (16-byte aligned)
+LRCCS_DEV void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+LRCCS_DEV bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit) {
+    unsigned done = 0;
+    for (unsigned it = 0; it < limit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
 // ---------------------------------------------------------------- FP32 r x r factorisation
 
 // In place A = L L^H for a Hermitian r x r A (FP32, row-major, r <= RMAX) by

@@ -25,7 +25,9 @@
 // Tiles are staged into shared memory with cp.async so that each thread keeps
 // many loads in flight; the transforms run on the staged tiles (fft.cuh).
 #include <cooperative_groups.h>
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched through the runtime)
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -52,13 +54,26 @@ int npairs_of(int r) { return r * (r + 1) / 2; }
 
 // ---------------------------------------------------------------- A: forward, along y
 
-template <int P>
+// The two tensor maps of a k_fwd_cols launch: U (rows of nx r complex, box
+// tx r complex x NY rows) and the coil maps (rows of nx complex over C ny
+// rows, box tx complex x NY rows).
+struct FwdMaps {
+    CUtensorMap u, s;
+};
+
+// With TMA, one thread loads the tile of U and of d_j as two tensor copies
+// (the tile layouts are the boxes' dense row-major layouts); otherwise every
+// thread issues 16-byte cp.async copies.
+template <int P, bool TMA>
 __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, const float2 *__restrict__ smaps,
                                                    const uint8_t *__restrict__ rowused, float2 *__restrict__ T,
                                                    int nx, int r, int tx, const float2 *__restrict__ g_tw,
-                                                   float scale) {
+                                                   float scale, const __grid_constant__ FwdMaps maps,
+                                                   unsigned int *status) {
     constexpr int NY = 32 * P;
-    extern __shared__ __align__(16) float2 smem[];
+    extern __shared__ __align__(128) float2 smem_raw[];
+    // 128-byte aligned start (a TMA destination); the launch adds 128 bytes of slack
+    float2 *smem = (float2 *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     float2 *tile = smem;                // NY * C
     float2 *sS = tile + NY * tx * r;    // NY * tx
     float2 *s_tw = sS + NY * tx;        // NY
@@ -68,21 +83,37 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
     // one copy unit = (row y, 16-byte piece); rows of U are C complex, of d_j tx
     // complex.  Every loop uses a fixed (column, row-step) thread mapping, so no
     // per-element division by the runtime row lengths.
-    const int upr = C / 2, spr = tx / 2;
+    const int upr = C / 2;
     const int uc = threadIdx.x % upr, uy = threadIdx.x / upr, ustep = blockDim.x / upr;
-    if (uy < ustep)
-        for (int y = uy; y < NY; y += ustep)
-            cp_async16(tile + y * C + 2 * uc, U + ((size_t)y * nx + x0) * r + 2 * uc);
-    {
-        const int sc = threadIdx.x % spr, sy = threadIdx.x / spr, sstep = blockDim.x / spr;
-        if (sy < sstep)
-            for (int y = sy; y < NY; y += sstep)
-                cp_async16(sS + y * tx + 2 * sc, smaps + (size_t)j * n + (size_t)y * nx + x0 + 2 * sc);
+    if constexpr (TMA) {
+        __shared__ __align__(8) uint64_t s_bar;
+        if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&s_bar, (unsigned)((NY * C + NY * tx) * sizeof(float2)));
+            tma_load_2d(tile, &maps.u, x0 * r * 2, 0, &s_bar);
+            tma_load_2d(sS, &maps.s, x0 * 2, j * NY, &s_bar);
+        }
+        load_twiddles(s_tw, g_tw, NY);
+        if (!mbar_wait(&s_bar, 0, 1u << 22) && threadIdx.x == 0) atomicOr(status, (unsigned)ST_TIMEOUT);
+        __syncthreads();
+    } else {
+        const int spr = tx / 2;
+        if (uy < ustep)
+            for (int y = uy; y < NY; y += ustep)
+                cp_async16(tile + y * C + 2 * uc, U + ((size_t)y * nx + x0) * r + 2 * uc);
+        {
+            const int sc = threadIdx.x % spr, sy = threadIdx.x / spr, sstep = blockDim.x / spr;
+            if (sy < sstep)
+                for (int y = sy; y < NY; y += sstep)
+                    cp_async16(sS + y * tx + 2 * sc, smaps + (size_t)j * n + (size_t)y * nx + x0 + 2 * sc);
+        }
+        cp_async_commit();
+        load_twiddles(s_tw, g_tw, NY);
+        cp_async_wait();
+        __syncthreads();
     }
-    cp_async_commit();
-    load_twiddles(s_tw, g_tw, NY);
-    cp_async_wait();
-    __syncthreads();
+
     {
         const int mc = threadIdx.x % C, my = threadIdx.x / C, mstep = blockDim.x / C, mcol = mc / r;
         if (my < mstep)
@@ -351,8 +382,8 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
 // Columns per k_fwd_cols tile: even, and tx r <= 64 when possible; or the
 // context's tuned plan (lrccs_autotune / lrccs_set_plan) when it fits.
 bool fwd_tile_ok(int tx, int r, int nx, int ny, int smem_optin) {
-    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
-    return tx >= 2 && (tx & 1) == 0 && nx % tx == 0 && tx * r <= 256 && smem <= (size_t)smem_optin;
+    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2) + 128;
+    return tx >= 2 && (tx & 1) == 0 && nx % tx == 0 && tx * r <= 256 && smem + 256 <= (size_t)smem_optin;
 }
 static int fwd_tile_x(const lrccs_ctx *c, int r) {
     if (c->plan.fwd_tx && fwd_tile_ok(c->plan.fwd_tx, r, c->nx, c->ny, c->dev_smem_optin)) return c->plan.fwd_tx;
@@ -379,16 +410,73 @@ static const row_w_t kRowW[RMAXC] = RANK_TABLE(k_row_w);
 
 // One launcher per iteration kernel, at the context's current rank c->r (the
 // _on / _to forms take the source or destination and the column count).
+// ---------------------------------------------------------------- tensor maps
+
+typedef CUresult (*encode_tiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link-time
+// dependence on libcuda); NULL when unavailable, and the callers then stage
+// with cp.async.
+static encode_tiled_t tensor_map_encoder() {
+    static const encode_tiled_t fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return (encode_tiled_t)p;
+    }();
+    return fn;
+}
+
+// A 2D FP32 tensor map: `outer` rows of `inner` floats, `row_bytes` apart,
+// copied in boxes of box_inner x box_outer.  False (nothing encoded) unless
+// every TMA rule holds: base and row pitch 16-byte aligned, box edges <= 256
+// with an inner extent of a multiple of 16 bytes.
+bool encode_map_2d(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                   uint32_t box_inner, uint32_t box_outer) {
+    const encode_tiled_t enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)base & 15) || (row_bytes & 15) || box_inner < 4 || box_inner > 256 || box_outer < 1 ||
+        box_outer > 256 || ((box_inner * 4) & 15) || box_inner > inner || box_outer > outer)
+        return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_fwd_cols_on(lrccs_ctx *c, const float2 *src, int r) {
     const int nx = c->nx, ny = c->ny;
     const float sy = (float)(1.0 / sqrt((double)ny));
     const int tx = fwd_tile_x(c, r);
-    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2);
+    // 128 bytes of slack: the TMA destination must start 128-byte aligned
+    const size_t smem = ((size_t)ny * tx * r + (size_t)ny * tx + ny) * sizeof(float2) + 128;
     dim3 grid(nx / tx, c->nc);
+    // the tiles by TMA when both maps encode (x offsets x0 r and x0 are even
+    // complex counts: 16-byte aligned, since tx is even)
+    FwdMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    const bool tma = (tx & 1) == 0 &&
+                     encode_map_2d(&maps.u, src, (uint64_t)nx * r * 2, (uint64_t)ny, (uint64_t)nx * r * 8,
+                                   (uint32_t)(tx * r * 2), (uint32_t)ny) &&
+                     encode_map_2d(&maps.s, c->d_smaps, (uint64_t)nx * 2, (uint64_t)c->nc * ny, (uint64_t)nx * 8,
+                                   (uint32_t)(tx * 2), (uint32_t)ny);
     DISPATCH_P(c->py, {
         prof_begin(c, KID_FWD_COLS);
-        k_fwd_cols<P_><<<grid, 256, smem, c->stream>>>(src, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
-                                                       c->d_twy, sy);
+        if (tma)
+            k_fwd_cols<P_, true><<<grid, 256, smem, c->stream>>>(src, c->d_smaps, c->d_rowused, c->d_T, nx, r, tx,
+                                                                 c->d_twy, sy, maps, c->d_status);
+        else
+            k_fwd_cols<P_, false><<<grid, 256, smem, c->stream>>>(src, c->d_smaps, c->d_rowused, c->d_T, nx, r,
+                                                                  tx, c->d_twy, sy, maps, c->d_status);
         prof_end(c, KID_FWD_COLS);
     });
     return cudaSuccess;
@@ -589,7 +677,12 @@ cudaError_t launch_images(lrccs_ctx *c, float2 *d_X) {
     SET_SMEM(fn<1>); SET_SMEM(fn<2>); SET_SMEM(fn<3>); SET_SMEM(fn<4>); \
     SET_SMEM(fn<5>); SET_SMEM(fn<6>); SET_SMEM(fn<7>); SET_SMEM(fn<8>)
 cudaError_t configure_kernels_iter(int max_smem) {
-    SET_SMEM_P(k_fwd_cols);
+    SET_SMEM(k_fwd_cols<1, false>); SET_SMEM(k_fwd_cols<2, false>); SET_SMEM(k_fwd_cols<3, false>);
+    SET_SMEM(k_fwd_cols<4, false>); SET_SMEM(k_fwd_cols<5, false>); SET_SMEM(k_fwd_cols<6, false>);
+    SET_SMEM(k_fwd_cols<7, false>); SET_SMEM(k_fwd_cols<8, false>);
+    SET_SMEM(k_fwd_cols<1, true>); SET_SMEM(k_fwd_cols<2, true>); SET_SMEM(k_fwd_cols<3, true>);
+    SET_SMEM(k_fwd_cols<4, true>); SET_SMEM(k_fwd_cols<5, true>); SET_SMEM(k_fwd_cols<6, true>);
+    SET_SMEM(k_fwd_cols<7, true>); SET_SMEM(k_fwd_cols<8, true>);
     for (int i = 0; i < RMAXC; ++i) {
         SET_SMEM(kRowGram[i]);
         SET_SMEM(kRowW[i]);
