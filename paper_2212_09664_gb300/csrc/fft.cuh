@@ -270,4 +270,105 @@ LRCCS_DEV void tile_dft(float2 *tile, int es, int ntrans, const float2 *__restri
     }
 }
 
+// The same transform with the tile's first read and last write replaced:
+// pass 1 reads element `row` of transform t as load(row, t) (e.g. the tile
+// times a coil map), and pass 2 hands each output (transform t, natural row,
+// unscaled value) to epi(t, row, v) instead of storing it into the tile (e.g.
+// a store to global memory, or an accumulation in registers).  Pass 2 only
+// reads the tile, so it has no barriers; a caller that reuses the tile after
+// it must synchronise.  Every thread of the block must call it.
+template <int N, bool INV, class LOAD, class EPI>
+LRCCS_DEV void tile_dft_io(float2 *tile, int es, int ntrans, const float2 *__restrict__ tw, LOAD load, EPI epi) {
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ngrp = nthr / ntrans;
+    const int t = tid % ntrans, g0 = tid / ntrans;
+    for (int j2 = (g0 < ngrp ? g0 : R2); j2 < R2; j2 += ngrp) {
+        float2 v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) v[m] = load(j2 + R2 * m, t);
+        Dft<R1, INV>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 w = tw[j2 * k1];
+            if (INV) w.y = -w.y;
+            tile[(j2 + R2 * k1) * es + t] = (k1 == 0) ? v[0] : cmul(v[k1], w);
+        }
+    }
+    __syncthreads();
+    const int tc = max(1, nthr / R1);
+    for (int t0 = 0; t0 < ntrans; t0 += tc) {
+        const int tn = min(tc, ntrans - t0);
+        if (tid < tn * R1) {
+            const int tt = t0 + tid % tn, k1 = tid / tn;
+            float2 v[R2];
+#pragma unroll
+            for (int j2 = 0; j2 < R2; ++j2) v[j2] = tile[(j2 + R2 * k1) * es + tt];
+            Dft<R2, INV>::run(v);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) epi(tt, k1 + R1 * k2, v[k2]);
+        }
+    }
+}
+
+// Pass 1 as in tile_dft (in place), then pass 2 hands every output to
+// epi(ch, k2, t, row, v) with the chunk ch < NCH and k2 < R2 as compile-time
+// constants after unrolling, so a caller can keep per-thread accumulators in
+// registers: a thread sees the same (t, row) for a given (ch, k2) on every
+// call with the same ntrans.  Requires ceil(ntrans / (blockDim.x / R1)) <= NCH.
+// Pass 2 only reads the tile (no barriers after pass 1).
+template <int N, bool INV, int NCH, class EPI>
+LRCCS_DEV void tile_dft_acc(float2 *tile, int es, int ntrans, const float2 *__restrict__ tw, EPI epi) {
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ngrp = nthr / ntrans;
+    const int t = tid % ntrans, g0 = tid / ntrans;
+    for (int j2 = (g0 < ngrp ? g0 : R2); j2 < R2; j2 += ngrp) {
+        float2 v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) v[m] = tile[(j2 + R2 * m) * es + t];
+        Dft<R1, INV>::run(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 w = tw[j2 * k1];
+            if (INV) w.y = -w.y;
+            tile[(j2 + R2 * k1) * es + t] = (k1 == 0) ? v[0] : cmul(v[k1], w);
+        }
+    }
+    __syncthreads();
+    const int tc = max(1, nthr / R1);
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        const int t0 = ch * tc;
+        const int tn = min(tc, ntrans - t0);
+        if (t0 < ntrans && tid < tn * R1) {
+            const int tt = t0 + tid % tn, k1 = tid / tn;
+            float2 v[R2];
+#pragma unroll
+            for (int j2 = 0; j2 < R2; ++j2) v[j2] = tile[(j2 + R2 * k1) * es + tt];
+            Dft<R2, INV>::run(v);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) epi(ch, k2, tt, k1 + R1 * k2, v[k2]);
+        }
+    }
+}
+
+// The (chunk, k2) -> (t, row) map of tile_dft_acc's pass 2 for this thread:
+// f(ch, k2, t, row) for every output it owns (e.g. to write its accumulators).
+template <int N, int NCH, class F>
+LRCCS_DEV void tile_dft_acc_slots(int ntrans, F f) {
+    constexpr int R1 = Plan<N>::R1, R2 = Plan<N>::R2;
+    const int tid = threadIdx.x, tc = max(1, (int)blockDim.x / R1);
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        const int t0 = ch * tc;
+        const int tn = min(tc, ntrans - t0);
+        if (t0 < ntrans && tid < tn * R1) {
+            const int tt = t0 + tid % tn, k1 = tid / tn;
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) f(ch, k2, tt, k1 + R1 * k2);
+        }
+    }
+}
+
 }  // namespace fft

@@ -114,18 +114,15 @@ __global__ void __launch_bounds__(256) k_fwd_cols(const float2 *__restrict__ U, 
         __syncthreads();
     }
 
-    {
-        const int mc = threadIdx.x % C, my = threadIdx.x / C, mstep = blockDim.x / C, mcol = mc / r;
-        if (my < mstep)
-            for (int y = my; y < NY; y += mstep) tile[y * C + mc] = cmul(sS[y * tx + mcol], tile[y * C + mc]);
-    }
-    __syncthreads();
-    fft::tile_dft<NY, false>(tile, C, C, s_tw, scale);
+    // F_y of d_j o U: the coil multiply happens as pass 1 reads the tile, and
+    // pass 2 stores the sampled rows straight to T
     float2 *Tj = T + ((size_t)j * n + x0) * r;
-    if (uy < ustep)
-        for (int ky = uy; ky < NY; ky += ustep)
-            if (rowused[ky])
-                *(float4 *)(Tj + (size_t)ky * nx * r + 2 * uc) = *(const float4 *)(tile + ky * C + 2 * uc);
+    const size_t rs = (size_t)nx * r;
+    fft::tile_dft_io<NY, false>(
+        tile, C, C, s_tw, [&](int y, int t) { return cmul(sS[y * tx + t / r], tile[y * C + t]); },
+        [&](int t, int ky, float2 v) {
+            if (rowused[ky]) Tj[(size_t)ky * rs + t] = cscale(v, scale);
+        });
 }
 
 // ---------------------------------------------------------------- B: row Gram
@@ -279,12 +276,13 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
 // registers; the CG partial tiles are then added through distributed shared
 // memory in rank order (deterministic), each block writing 1/CG of the column.
 
-template <int P, int EA>   // EA: output tile elements per thread, NY r <= 256 EA
+template <int P, int NCH>   // NCH: pass-2 chunks of the 2r transforms (1 or 2)
 __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
                                                    const uint8_t *__restrict__ rowused, float2 *__restrict__ Gk,
                                                    int nx, int r, int nc, const float2 *__restrict__ g_tw,
                                                    float scale) {
     constexpr int NY = 32 * P;
+    constexpr int R2 = fft::Plan<NY>::R2;
     extern __shared__ __align__(16) float2 smem[];
     // two coils per transform call: tile[y][c r + l], c = 0, 1 (two buffers)
     float2 *tile0 = smem;                 // NY * 2r
@@ -296,17 +294,18 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
     const int x = blockIdx.x, g = blockIdx.y, CG = gridDim.y;
     const size_t n = (size_t)NY * nx;
     const int cnt = NY * r, r2 = 2 * r;
-    // this thread's output elements e = tid + 256 u hold (y, l) = (yy[u], e - yy[u] r);
     // rows that no frame samples are zero-filled
     __shared__ uint8_t s_used[32 * 8];
     for (int y = threadIdx.x; y < NY; y += blockDim.x) s_used[y] = rowused[y];
-    float2 acc[EA];
-    int yy[EA];
+    // staging map: thread -> rank index l, rows y0, y0 + ystep, ...
+    const int sl = threadIdx.x % r, sy0 = threadIdx.x / r, systep = blockDim.x / r;
+    // pass-2 accumulators: conj(d_j) F_y^H of every coil of this block, per
+    // (chunk, k2) output of tile_dft_acc (a fixed (t, row) per thread)
+    float2 acc[NCH][R2];
 #pragma unroll
-    for (int u = 0; u < EA; ++u) {
-        acc[u] = make_float2(0.f, 0.f);
-        yy[u] = (threadIdx.x + 256 * u) / r;
-    }
+    for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) acc[ch][k2] = make_float2(0.f, 0.f);
     __syncthreads();
     // coils of this block: g, g + CG, g + 2 CG, ...; step s takes the pair (2s, 2s + 1) of them
     const int mine = g < nc ? (nc - 1 - g) / CG + 1 : 0;
@@ -318,16 +317,12 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
             const int j = g + m * CG;
             const bool live = m < mine;
             const float2 *Tj = T + (size_t)j * n * r + (size_t)x * r;
-#pragma unroll
-            for (int u = 0; u < EA; ++u) {
-                const int e = threadIdx.x + 256 * u;
-                if (e < cnt) {
-                    const int y = yy[u], l = e - y * r;
-                    float2 *dst = tile + y * r2 + c * r + l;
-                    if (live && s_used[y]) cp_async8(dst, Tj + (size_t)y * nx * r + l);
+            if (sy0 < systep)
+                for (int y = sy0; y < NY; y += systep) {
+                    float2 *dst = tile + y * r2 + c * r + sl;
+                    if (live && s_used[y]) cp_async8(dst, Tj + (size_t)y * nx * r + sl);
                     else *dst = make_float2(0.f, 0.f);
                 }
-            }
             for (int y = threadIdx.x; y < NY; y += blockDim.x) {
                 if (live) cp_async8(sS + c * NY + y, smaps + (size_t)j * n + (size_t)y * nx + x);
                 else sS[c * NY + y] = make_float2(0.f, 0.f);
@@ -347,23 +342,17 @@ __global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, 
             cp_async_wait();
         }
         __syncthreads();
-        fft::tile_dft<NY, true>(tile, r2, r2, s_tw, scale);
-#pragma unroll
-        for (int u = 0; u < EA; ++u) {
-            const int e = threadIdx.x + 256 * u;
-            if (e < cnt) {
-                const int y = yy[u], l = e - y * r;
-                cfmac(acc[u], sS[y], tile[y * r2 + l]);
-                cfmac(acc[u], sS[NY + y], tile[y * r2 + r + l]);
-            }
-        }
+        fft::tile_dft_acc<NY, true, NCH>(tile, r2, r2, s_tw, [&](int ch, int k2, int t, int y, float2 v) {
+            cfmac(acc[ch][k2], sS[(t >= r ? NY : 0) + y], cscale(v, scale));
+        });
         __syncthreads();
     }
-    // partial tile of this block into its own tile0, then the cluster-wide sum
-#pragma unroll
-    for (int u = 0; u < EA; ++u) {
-        const int e = threadIdx.x + 256 * u;
-        if (e < cnt) tile0[e] = acc[u];
+    // this block's partial column: the two coil halves added, into tile0[y r + l]
+    fft::tile_dft_acc_slots<NY, NCH>(r2, [&](int ch, int k2, int t, int y) { tile1[y * r2 + t] = acc[ch][k2]; });
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int y = e / r, l = e - y * r;
+        tile0[e] = cadd(tile1[y * r2 + l], tile1[y * r2 + r + l]);
     }
     cluster.sync();
     const int per = (cnt + CG - 1) / CG;
@@ -532,15 +521,18 @@ cudaError_t launch_adj_cols_to(lrccs_ctx *c, float2 *dst, int r) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const bool small = ny * r <= 256 * 8;
+    // pass-2 chunks of the 2r transforms: 256 / R1 transforms per chunk
+    static const int kR1[9] = {0, 4, 8, 12, 8, 10, 12, 14, 16};   // fft::Plan<32 P>::R1
+    const int nch = (2 * r + 256 / kR1[c->py] - 1) / (256 / kR1[c->py]);
+    if (nch > 2) return cudaErrorInvalidValue;
     cudaError_t el = cudaSuccess;
     DISPATCH_P(c->py, {
         prof_begin(c, KID_ADJ_COLS);
-        if (small)
-            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 8>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+        if (nch == 1)
+            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 1>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
                                     (const uint8_t *)c->d_rowused, dst, nx, r, c->nc, (const float2 *)c->d_twy, sy);
         else
-            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 16>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
+            el = cudaLaunchKernelEx(&cfg, k_adj_cols<P_, 2>, (const float2 *)c->d_T, (const float2 *)c->d_smaps,
                                     (const uint8_t *)c->d_rowused, dst, nx, r, c->nc, (const float2 *)c->d_twy, sy);
         prof_end(c, KID_ADJ_COLS);
     });
@@ -687,9 +679,9 @@ cudaError_t configure_kernels_iter(int max_smem) {
         SET_SMEM(kRowGram[i]);
         SET_SMEM(kRowW[i]);
     }
-    SET_SMEM(k_adj_cols<1, 8>); SET_SMEM(k_adj_cols<2, 8>); SET_SMEM(k_adj_cols<3, 8>); SET_SMEM(k_adj_cols<4, 8>);
-    SET_SMEM(k_adj_cols<5, 8>); SET_SMEM(k_adj_cols<6, 8>); SET_SMEM(k_adj_cols<7, 8>); SET_SMEM(k_adj_cols<8, 8>);
-    SET_SMEM(k_adj_cols<1, 16>); SET_SMEM(k_adj_cols<2, 16>); SET_SMEM(k_adj_cols<3, 16>); SET_SMEM(k_adj_cols<4, 16>);
-    SET_SMEM(k_adj_cols<5, 16>); SET_SMEM(k_adj_cols<6, 16>); SET_SMEM(k_adj_cols<7, 16>); SET_SMEM(k_adj_cols<8, 16>);
+    SET_SMEM(k_adj_cols<1, 1>); SET_SMEM(k_adj_cols<2, 1>); SET_SMEM(k_adj_cols<3, 1>); SET_SMEM(k_adj_cols<4, 1>);
+    SET_SMEM(k_adj_cols<5, 1>); SET_SMEM(k_adj_cols<6, 1>); SET_SMEM(k_adj_cols<7, 1>); SET_SMEM(k_adj_cols<8, 1>);
+    SET_SMEM(k_adj_cols<1, 2>); SET_SMEM(k_adj_cols<2, 2>); SET_SMEM(k_adj_cols<3, 2>); SET_SMEM(k_adj_cols<4, 2>);
+    SET_SMEM(k_adj_cols<5, 2>); SET_SMEM(k_adj_cols<6, 2>); SET_SMEM(k_adj_cols<7, 2>); SET_SMEM(k_adj_cols<8, 2>);
     return cudaSuccess;
 }
