@@ -438,11 +438,17 @@ extern "C" lrccs_status lrccs_init(lrccs_ctx *c, const void *d_y, const int64_t 
     lrccs_status s = load_data(c, d_y, d_frame_ptr, d_mask, d_smaps, true);
     if (s != LRCCS_OK) return s;
     CK(launch_gram_x0(c));
-    s = sync_status(c);
-    if (s != LRCCS_OK) return s;
-    int32_t meta[MT_COUNT];
-    CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
-    c->r = meta[MT_RANK];
+    if (c->dims.rank > 0 && c->dims.rank <= c->rmax) {
+        // a fixed rank: the kernels after the eigensolver need no host decision,
+        // so its status is read by the final synchronisation
+        c->r = c->dims.rank;
+    } else {
+        s = sync_status(c);
+        if (s != LRCCS_OK) return s;
+        int32_t meta[MT_COUNT];
+        CK(cudaMemcpy(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost));
+        c->r = meta[MT_RANK];
+    }
     if (c->r < 1 || c->r > c->rmax) {
         set_err(c, "lrccs_init: rank %d outside [1, rank_max=%d]", c->r, c->rmax);
         return LRCCS_E_INVALID;

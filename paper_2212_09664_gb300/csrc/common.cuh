@@ -91,15 +91,22 @@ LRCCS_DEV bool last_block_arrive(unsigned int *counter) {
 // removes the phase of a_pq and applies the real 2x2 Jacobi rotation:
 // G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]], A <- G^H A G, V <- V G.
 // V (ldv columns, may be global memory) is updated when non-null.
-// A rotation is skipped when |a_pq| <= rel_tol sqrt(|a_pp a_qq|) or |a_pq| <= abs_tol;
+// A rotation is skipped when |a_pq| <= rel_tol sqrt(|a_pp a_qq|) or |a_pq| <= abs_tol,
+// or when both |a_pp| and |a_qq| are below tail_tol (a rotation between two
+// such indices only mixes columns p and q of V: when every wanted eigenvalue
+// is above tail_tol, the wanted eigenvectors converge without them);
 // the sweeps stop when a whole sweep skips every rotation.
 __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ldv, float *s_c, float *s_s, float2 *s_e,
-                             int *s_cnt, int max_sweeps, float abs_tol = 0.f, float rel_tol = 1e-7f) {
+                             int *s_cnt, int max_sweeps, float abs_tol = 0.f, float rel_tol = 1e-7f,
+                             float tail_tol = 0.f) {
     const int n2 = n + (n & 1);
     const int npair = n2 / 2;
     int sh = 0;                             // column index stride 2^sh >= n (no division per task)
     while ((1 << sh) < n) ++sh;
     const int mmask = (1 << sh) - 1;
+    int psh = 0;                            // pair index stride 2^psh >= npair
+    while ((1 << psh) < npair) ++psh;
+    const int pmask = (1 << psh) - 1;
     __shared__ short s_pp[64], s_qq[64];   // the pairs of the current round
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *s_cnt = 0;
@@ -117,7 +124,8 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
                     const float2 apq = A[p * lda + qq];
                     const float b2 = apq.x * apq.x + apq.y * apq.y;
                     const float al = A[p * lda + p].x, ga = A[qq * lda + qq].x;
-                    if (b2 > 1e-36f && b2 > abs_tol * abs_tol && b2 > rel_tol * rel_tol * fabsf(al) * fabsf(ga)) {
+                    if (b2 > 1e-36f && b2 > abs_tol * abs_tol && b2 > rel_tol * rel_tol * fabsf(al) * fabsf(ga) &&
+                        (fabsf(al) >= tail_tol || fabsf(ga) >= tail_tol)) {
                         // the rotation only has to be orthogonal: c = 1 / sqrt(1 + t^2),
                         // s = t c hold to rounding whatever the accuracy of t
                         const float ib = rsqrtf(b2);
@@ -134,33 +142,55 @@ __device__ inline void block_jacobi(float2 *A, int n, int lda, float2 *V, int ld
                 s_e[i] = e;
             }
             __syncthreads();
-            // rows p, q: A <- G^H A
-            for (int task = threadIdx.x; task < (npair << sh); task += blockDim.x) {
-                const int i = task >> sh, m = task & mmask;
-                if (m >= n || s_s[i] == 0.f) continue;
-                const int p = s_pp[i], qq = s_qq[i];
-                const float c = s_c[i], s = s_s[i];
-                const float2 e = s_e[i];
-                const float2 ap = A[p * lda + m], aq = A[qq * lda + m];
-                const float2 eaq = cmul(e, aq);
-                A[p * lda + m] = make_float2(c * ap.x - s * eaq.x, c * ap.y - s * eaq.y);
-                A[qq * lda + m] = make_float2(s * ap.x + c * eaq.x, s * ap.y + c * eaq.y);
-            }
-            __syncthreads();
-            // columns p, q: A <- A G ; V <- V G
-            for (int task = threadIdx.x; task < (npair << sh); task += blockDim.x) {
-                const int i = task >> sh, m = task & mmask;
-                if (m >= n || s_s[i] == 0.f) continue;
-                const int p = s_pp[i], qq = s_qq[i];
-                const float c = s_c[i], s = s_s[i];
-                const float2 eh = cconj(s_e[i]);
-                {
-                    const float2 ap = A[m * lda + p], aq = A[m * lda + qq];
-                    const float2 e2 = cmul(eh, aq);
-                    A[m * lda + p] = make_float2(c * ap.x - s * e2.x, c * ap.y - s * e2.y);
-                    A[m * lda + qq] = make_float2(s * ap.x + c * e2.x, s * ap.y + c * e2.y);
-                }
-                if (V) {
+            // A <- G^H A G on the 2 x 2 blocks (rows of pair i, columns of
+            // pair i2: disjoint, so one pass; the row rotation first, then
+            // the column rotation, as two separate passes would), and V <- V G
+            const int nab = npair << psh;
+            for (int task = threadIdx.x; task < nab + (V ? (npair << sh) : 0); task += blockDim.x) {
+                if (task < nab) {
+                    const int i = task >> psh, i2 = task & pmask;
+                    if (i2 >= npair) continue;
+                    const float si = s_s[i], si2 = s_s[i2];
+                    if (si == 0.f && si2 == 0.f) continue;
+                    const int p = s_pp[i], qq = s_qq[i], p2 = s_pp[i2], q2 = s_qq[i2];
+                    const bool r0 = p < n, r1 = qq < n, c0 = p2 < n, c1 = q2 < n;
+                    const float2 z = make_float2(0.f, 0.f);
+                    float2 a00 = r0 && c0 ? A[p * lda + p2] : z, a01 = r0 && c1 ? A[p * lda + q2] : z;
+                    float2 a10 = r1 && c0 ? A[qq * lda + p2] : z, a11 = r1 && c1 ? A[qq * lda + q2] : z;
+                    if (si != 0.f) {   // rows p, q of columns p2, q2
+                        const float c = s_c[i];
+                        const float2 e = s_e[i];
+                        float2 eaq = cmul(e, a10);
+                        float2 ap = a00;
+                        a00 = make_float2(c * ap.x - si * eaq.x, c * ap.y - si * eaq.y);
+                        a10 = make_float2(si * ap.x + c * eaq.x, si * ap.y + c * eaq.y);
+                        eaq = cmul(e, a11);
+                        ap = a01;
+                        a01 = make_float2(c * ap.x - si * eaq.x, c * ap.y - si * eaq.y);
+                        a11 = make_float2(si * ap.x + c * eaq.x, si * ap.y + c * eaq.y);
+                    }
+                    if (si2 != 0.f) {   // columns p2, q2 of rows p, q
+                        const float c = s_c[i2];
+                        const float2 eh = cconj(s_e[i2]);
+                        float2 e2 = cmul(eh, a01);
+                        float2 ap = a00;
+                        a00 = make_float2(c * ap.x - si2 * e2.x, c * ap.y - si2 * e2.y);
+                        a01 = make_float2(si2 * ap.x + c * e2.x, si2 * ap.y + c * e2.y);
+                        e2 = cmul(eh, a11);
+                        ap = a10;
+                        a10 = make_float2(c * ap.x - si2 * e2.x, c * ap.y - si2 * e2.y);
+                        a11 = make_float2(si2 * ap.x + c * e2.x, si2 * ap.y + c * e2.y);
+                    }
+                    if (r0 && c0) A[p * lda + p2] = a00;
+                    if (r0 && c1) A[p * lda + q2] = a01;
+                    if (r1 && c0) A[qq * lda + p2] = a10;
+                    if (r1 && c1) A[qq * lda + q2] = a11;
+                } else {
+                    const int tv = task - nab, i = tv >> sh, m = tv & mmask;
+                    if (m >= n || s_s[i] == 0.f) continue;
+                    const int p = s_pp[i], qq = s_qq[i];
+                    const float c = s_c[i], s = s_s[i];
+                    const float2 eh = cconj(s_e[i]);
                     const float2 vp = V[m * ldv + p], vq = V[m * ldv + qq];
                     const float2 e2 = cmul(eh, vq);
                     V[m * ldv + p] = make_float2(c * vp.x - s * e2.x, c * vp.y - s * e2.y);

@@ -496,15 +496,36 @@ __global__ void k_eig(const double *__restrict__ gram, int q, int n, int nc, int
     fro = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fro += s_fro[w];
     if (!refine) {
-        // a rotation is skipped once |a_pq| <= 1e-6 sqrt(a_pp a_qq) or <= 1e-7
-        // ||A||_F: FP32 rounding keeps regenerating off-diagonal entries near
-        // that floor, which the refine pass removes
-        block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 8, (float)(1e-7 * sqrt(fro)), 1e-6f);
+        // a rotation is skipped once |a_pq| <= 1e-5 sqrt(a_pp a_qq) or <= 1e-6
+        // ||A||_F, at most 5 sweeps: this pass only has to leave B = V0^H A V0
+        // diagonally dominant; the refine pass converges quadratically from there
+        block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 5, (float)(1e-6 * sqrt(fro)), 1e-5f);
         if (v_in_smem)
             for (int e = threadIdx.x; e < q * q; e += blockDim.x) V[e] = Vw[(e / q) * ldv + e % q];
         return;
     }
-    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 6, 0.f, 1e-6f);
+    // the wanted eigenpairs: the top rank_in (fixed rank) or the rank rule's
+    // cap; rotations between two indices whose diagonal entries are both
+    // below a quarter of the r_w-th largest entry cannot change them
+    __shared__ float s_tail;
+    {
+        int capn = min(n, q);
+        const long long cm = (long long)nc * meta[MT_MMIN];
+        if (cm < capn) capn = (int)cm;
+        const int cap = max(1, capn / 10);
+        const int rw = min(q, max(rank_in, cap));
+        for (int i = threadIdx.x; i < q; i += blockDim.x) {
+            const float di = sA[i * ld + i].x;
+            int above = 0;
+            for (int j = 0; j < q; ++j) {
+                const float dj = sA[j * ld + j].x;
+                above += (dj > di || (dj == di && j < i)) ? 1 : 0;
+            }
+            if (above == rw - 1) s_tail = 0.25f * di;
+        }
+        __syncthreads();
+    }
+    block_jacobi(sA, q, ld, Vw, ldv, s_c, s_s, s_e, &s_cnt, 6, 0.f, 1e-6f, s_tail);
     // eigenvalues (diagonal of the rotated B, scaled back), then V <- V0 Q,
     // formed in the shared A region (A is no longer needed)
     for (int i = threadIdx.x; i < q; i += blockDim.x) s_lam[i] = sA[i * ld + i].x;
