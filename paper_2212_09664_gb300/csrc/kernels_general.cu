@@ -217,7 +217,10 @@ __global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ 
     float2 *s_y = s_twy + NY;             // IG_STAGE staged samples of one coil
     int16_t *s_kx = (int16_t *)(s_y + IG_STAGE);
     uint8_t *s_tr = (uint8_t *)(s_kx + IG_STAGE);
-    __shared__ int s_grp[3];
+    // the frame's rows (the same for every coil): row ky, sample count and
+    // first sample, and the row groups whose samples fit the staging area
+    __shared__ int s_ky[NY], s_rc[NY], s_ro[NY], s_gb[NY + 1];
+    __shared__ int s_ng;
     const int k = blockIdx.y, x0 = blockIdx.x * TXG;
     const int n = NY * nx;
     load_twiddles(s_twy, g_twy, NY);
@@ -227,6 +230,27 @@ __global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ 
     }
     const int lp = lineptr[k], L = lineptr[k + 1] - lp;
     const int f0 = fpk[k], mk = mks[k];
+    for (int li = threadIdx.x; li < L; li += blockDim.x) {
+        const int ky = framerows[lp + li];
+        s_ky[li] = ky;
+        s_rc[li] = rowcnt[k * NY + ky];
+        s_ro[li] = rowoff[k * NY + ky];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ng = 0, tot = 0;
+        s_gb[0] = 0;
+        for (int li = 0; li < L; ++li) {
+            const int c = s_rc[li];
+            if (li > 0 && tot + c > IG_STAGE) {
+                s_gb[++ng] = li;
+                tot = 0;
+            }
+            tot += c;
+        }
+        if (L > 0) s_gb[++ng] = L;
+        s_ng = ng;
+    }
     float2 acc[ACC];
 #pragma unroll
     for (int u = 0; u < ACC; ++u) acc[u] = make_float2(0.f, 0.f);
@@ -235,22 +259,10 @@ __global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ 
         for (int e = threadIdx.x; e < NY * TP; e += blockDim.x) tile[e] = make_float2(0.f, 0.f);
         const int64_t yb = (int64_t)nc * f0 + (int64_t)j * mk;   // sample f0 + s of coil j at y[yb + s]
         // the frame's rows in groups whose samples fit the staging area
-        for (int g0 = 0; g0 < L;) {
+        for (int gi = 0; gi < s_ng; ++gi) {
             __syncthreads();
-            if (threadIdx.x == 0) {
-                int g1 = g0, tot = 0;
-                while (g1 < L) {
-                    const int c = rowcnt[k * NY + framerows[lp + g1]];
-                    if (g1 > g0 && tot + c > IG_STAGE) break;
-                    tot += c;
-                    ++g1;
-                }
-                s_grp[0] = g1;
-                s_grp[1] = rowoff[k * NY + framerows[lp + g0]];
-                s_grp[2] = tot;
-            }
-            __syncthreads();
-            const int g1 = s_grp[0], sbase = s_grp[1], scnt = s_grp[2];
+            const int g0 = s_gb[gi], g1 = s_gb[gi + 1];
+            const int sbase = s_ro[g0], scnt = s_ro[g1 - 1] + s_rc[g1 - 1] - sbase;
             // stage the group's samples of coil j: value, kx, and the truncation
             // flag (1: |y|^2 > gamma, dropped from the truncated copy)
             for (int e = threadIdx.x; e < scnt; e += blockDim.x) {
@@ -263,8 +275,8 @@ __global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ 
             // item (row li, column quad cq): columns x0 + 4 cq .. x0 + 4 cq + 3
             for (int e = threadIdx.x; e < (g1 - g0) * (TXG / 4); e += blockDim.x) {
                 const int li = g0 + e / (TXG / 4), cq = e % (TXG / 4);
-                const int ky = framerows[lp + li];
-                const int off = rowoff[k * NY + ky] - sbase, cnt = rowcnt[k * NY + ky];
+                const int ky = s_ky[li];
+                const int off = s_ro[li] - sbase, cnt = s_rc[li];
                 float2 vp[4], vt[4];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) vp[jj] = vt[jj] = make_float2(0.f, 0.f);
@@ -287,7 +299,6 @@ __global__ void __launch_bounds__(256, 2) k_init_gen(const float2 *__restrict__ 
                     tile[ky * TP + 2 * (4 * cq + jj) + 1] = cscale(vt[jj], sx);
                 }
             }
-            g0 = g1;
         }
         __syncthreads();
         fft::tile_dft<NY, true>(tile, TP, 2 * TXG, s_twy, sy);
