@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(256) k_row_w(float2 *__restrict__ T, const flo
 // registers; the CG partial tiles are then added through distributed shared
 // memory in rank order (deterministic), each block writing 1/CG of the column.
 
+// (two chunks: registers capped for two blocks per SM; a third block per SM
+// made the one-chunk form slower)
 template <int P, int NCH>   // NCH: pass-2 chunks of the 2r transforms (1 or 2)
-__global__ void __launch_bounds__(256) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
+__global__ void __launch_bounds__(256, NCH == 2 ? 2 : 1) k_adj_cols(const float2 *__restrict__ T, const float2 *__restrict__ smaps,
                                                    const uint8_t *__restrict__ rowused, float2 *__restrict__ Gk,
                                                    int nx, int r, int nc, const float2 *__restrict__ g_tw,
                                                    float scale) {
