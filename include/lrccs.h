@@ -419,12 +419,11 @@ lrccs_status lrccs_profile_reset(lrccs_ctx *ctx);
  * It allocates nothing and calls no allocating routine.  Its scratch is a
  * fixed array in device memory at file scope (one FP64 partial sum per 65,536
  * entries, 4,096 at most, plus a counter: 32 KiB + 256 B) that every device
- * which loads the library holds until the process exits.  The first call on a
- * device looks up that array's device address with the device current (a
- * cudaGetSymbolAddress), so make the first call on each device before any
- * stream capture.  The address is kept for the life of the process, so this
- * entry point must not be used on a device after cudaDeviceReset (which
- * reloads the library's device code at a new address).  Every call shares the
+ * which loads the library holds until the process exits.  Every call looks up
+ * that array's device address in the current context (cudaGetSymbolAddress,
+ * which allocates nothing), so the entry point also works after a context is
+ * recreated (cudaDeviceReset); make the first call on each device before any
+ * stream capture (the first lookup loads the module).  Every call shares the
  * array and clears its counter before
  * use; calls whose work overlaps on the GPU (different streams, or another
  * host thread) race on it and must be serialised by the caller.

@@ -6,7 +6,6 @@
 // lrccs_create allocates.  This file provides the same reduction for callers
 // that must not allocate: its scratch is a fixed-size array at file scope in
 // device memory, present on every device that loads the library.
-#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -57,11 +56,6 @@ __global__ void __launch_bounds__(NA_THREADS) k_energy_noalloc(const float2 *__r
     }
 }
 
-// Device address of g_na_scratch, resolved once per device and kept for the
-// life of the process (a cudaDeviceReset would move it; the header forbids
-// calls after one).
-static std::mutex g_na_mutex;
-static na_scratch *g_na_addr[256];
 
 extern "C" lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t count, double trunc_factor,
                                                       double *d_gamma, void *cuda_stream) {
@@ -81,23 +75,15 @@ extern "C" lrccs_status lrccs_trunc_threshold_noalloc(const void *d_y, int64_t c
         set_err(nullptr, "lrccs_trunc_threshold_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
         return LRCCS_E_CUDA;
     }
-    na_scratch *scr = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_addr[dev]) {
-            // First call on this device: with the device current, turn the
-            // host-side name of the array into its device address.
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_na_scratch);
-            if (e != cudaSuccess || !p) {
-                set_err(nullptr, "lrccs_trunc_threshold_noalloc: cudaGetSymbolAddress failed: %s",
-                        cudaGetErrorString(e));
-                return LRCCS_E_CUDA;
-            }
-            g_na_addr[dev] = (na_scratch *)p;
-        }
-        scr = g_na_addr[dev];
+    // the device address of the array in the current context, resolved on
+    // every call (no allocation; stays right after a context is recreated)
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess || !p) {
+        set_err(nullptr, "lrccs_trunc_threshold_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return LRCCS_E_CUDA;
     }
+    na_scratch *scr = (na_scratch *)p;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // The counter must start at zero; the partial sums are overwritten.
     e = cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned int), s);
