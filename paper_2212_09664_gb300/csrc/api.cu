@@ -91,7 +91,8 @@ static void free_all(lrccs_ctx *c) {
                     c->d_mks, c->d_fpk, c->d_rowoff, c->d_ucnt, c->d_uloc, c->d_floc, c->d_urow, c->d_uptr,
                     c->d_ufrow, c->d_upos, c->d_uidx, c->d_ufptr, c->d_uflist, c->d_fu, c->d_FU, c->d_Pu,
                     c->d_maskc, c->d_mec, c->d_mscal, c->d_mout, c->d_twq, c->d_Q, c->d_gdts, c->d_fpart,
-                    c->d_tflag, c->d_tcA0, c->d_tcA1, c->d_tcscale, c->d_ZB, c->d_hpart};
+                    c->d_tflag, c->d_tcA0, c->d_tcA1, c->d_tcscale, c->d_ZB, c->d_hpart,
+                    c->d_tcB0, c->d_tcB1};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -193,6 +194,8 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
         {(void **)&c->d_maskc, (size_t)q * n}, {(void **)&c->d_twq, (size_t)q * F2},
         {(void **)&c->d_tcA0, d.precision != LRCCS_PREC_FP32_FFT ? tc_a_elems(ny) * 2 : 0},
         {(void **)&c->d_tcA1, d.precision == LRCCS_PREC_BF16X3_GEMM ? tc_a_elems(ny) * 2 : 0},
+        {(void **)&c->d_tcB0, d.precision != LRCCS_PREC_FP32_FFT ? tc_b_elems(nc, ny, c->nx, rmax) * 2 : 0},
+        {(void **)&c->d_tcB1, d.precision == LRCCS_PREC_BF16X3_GEMM ? tc_b_elems(nc, ny, c->nx, rmax) * 2 : 0},
         {(void **)&c->d_tcscale, (1 + ((size_t)c->nx * rmax + 127) / 128) * sizeof(float)},
     };
     size_t need = 0;
@@ -1272,7 +1275,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_scale", "k_zb"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_max", "k_b_operand", "k_zb"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {

@@ -49,7 +49,7 @@ enum {
     // model-error correction (Alg. 3) and online tracking (Alg. 5)
     KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT,
     // precision forms of the forward transform (tcgen05 GEMM)
-    KID_TC_A, KID_TC_GEMM, KID_TC_SCALE,
+    KID_TC_A, KID_TC_GEMM, KID_TC_SCALE, KID_TC_B,
     // Z B^H of the gradient
     KID_ZB, KID_COUNT
 };
@@ -188,7 +188,8 @@ struct lrccs_ctx {
     // precision forms: the DFT matrix of the sampled rows as tensor-core
     // operand tiles (bf16 hi / lo, or fp16 in d_tcA0)
     uint16_t *d_tcA0, *d_tcA1;
-    float *d_tcscale;            // FP16S: [0] max over the coil maps, then one scale per N tile
+    uint16_t *d_tcB0, *d_tcB1;   // the B operand d_j o U in the same tiled layout (k_b_operand)
+    float *d_tcscale;            // FP16S: [0] max |d| over the coil maps, then max |U| entry per N tile
     float2 *d_twq;               // q twiddles exp(-2 pi i t / q) of the temporal DFT
     int mec_w, mec_nch;
 };
@@ -232,6 +233,7 @@ cudaError_t launch_dft_a(lrccs_ctx *c);
 cudaError_t launch_forward(lrccs_ctx *c);   // the iteration's forward transform of U (FFT or GEMM)
 cudaError_t launch_fwd_gemm(lrccs_ctx *c);
 size_t tc_a_elems(int ny);
+size_t tc_b_elems(int nc, int ny, int nx, int rmax);
 cudaError_t launch_energy(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_init_adjoint(lrccs_ctx *c, const float2 *d_y);
 cudaError_t launch_gram_x0(lrccs_ctx *c);
