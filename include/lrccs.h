@@ -68,7 +68,8 @@ typedef enum lrccs_status {
  * dense GEMM with the DFT matrix of the sampled rows on the tcgen05 tensor
  * cores, accumulating in FP32 (Sec. II-A's A_k U, F as a matrix):
  *   BF16X3: operands split into bf16 hi + lo, three products (hi hi, hi lo, lo hi);
- *   FP16S : one FP16 product, the U-side tile scaled per CTA by a power of two.
+ *   FP16S : one FP16 product, the U-side operand scaled per 128-column tile by
+ *           a power of two (from the tile's largest entry), unscaled after.
  * Everything else (the adjoint, the Grams, the solves, the QR, the init) is
  * the same in every form.  Other values: LRCCS_E_UNSUPPORTED. */
 typedef enum lrccs_precision {
