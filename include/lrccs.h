@@ -392,7 +392,8 @@ lrccs_status lrccs_set_state(lrccs_ctx *ctx, const void *host_buf, size_t bytes)
  * totals and fills up to `max` entries of `out` (one per kernel, in a fixed
  * order); *count receives the number of kernels.  Names are static strings.
  * Inside a replayed iteration graph (lrccs_iterate) the event records are graph
- * nodes placed on every 8th iteration (the `timed` count says how many), and
+ * nodes placed on captured iterations 8, 24, 40, ... counted from 0 (the
+ * `timed` count says how many), and
  * every replay since the last read reports the timings of the latest replay. */
 typedef struct lrccs_kernel_stat {
     const char *name;     /* kernel name */

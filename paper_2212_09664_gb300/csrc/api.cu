@@ -538,7 +538,7 @@ static bool ensure_iter_graph(lrccs_ctx *c, int n_iter) {
         c->capturing = true;
         cudaError_t el = cudaSuccess;
         for (int it = 0; it < n_iter && el == cudaSuccess; ++it) {
-            c->capture_iter = it;   // timing events on every 8th captured iteration
+            c->capture_iter = it;   // timing events on captured iterations 8, 24, 40, ...
             el = launch_iteration(c);
         }
         c->capturing = false;
@@ -1290,7 +1290,7 @@ static cudaEvent_t get_event(lrccs_ctx *c) {
 
 void prof_begin(lrccs_ctx *c, int kid) {
     c->launches[kid] += 1;
-    c->prof_this = (c->prof_mask & (1ull << kid)) && !(c->capturing && (c->capture_iter & 7) != 0);
+    c->prof_this = (c->prof_mask & (1ull << kid)) && !(c->capturing && (c->capture_iter & 15) != 8);
     if (c->prof_this) {
         prof_rec r;
         r.kid = kid;

@@ -496,11 +496,24 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
             for (int ii = hs; ii < cn; ii += Sh) {
                 const float4 z = *(const float4 *)(s_z + ii * zs + hk);   // Z[k], Z[k+1] (pad column when k+1 = q)
                 const float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
+                if constexpr ((R & 1) == 0) {   // U_{t+1} row in 16-byte pairs (r even: rows 16-byte aligned)
+                    const float4 *u4 = (const float4 *)(s_a + ii * r);
 #pragma unroll
-                for (int l = 0; l < R; ++l) {
-                    const float2 u = s_a[ii * r + l];
-                    cfmac(pv[l], u, z0);
-                    cfmac(pv[R + l], u, z1);
+                    for (int l2 = 0; l2 < R / 2; ++l2) {
+                        const float4 uu = u4[l2];
+                        const float2 ua = make_float2(uu.x, uu.y), ub = make_float2(uu.z, uu.w);
+                        cfmac(pv[2 * l2], ua, z0);
+                        cfmac(pv[R + 2 * l2], ua, z1);
+                        cfmac(pv[2 * l2 + 1], ub, z0);
+                        cfmac(pv[R + 2 * l2 + 1], ub, z1);
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < R; ++l) {
+                        const float2 u = s_a[ii * r + l];
+                        cfmac(pv[l], u, z0);
+                        cfmac(pv[R + l], u, z1);
+                    }
                 }
             }
         }

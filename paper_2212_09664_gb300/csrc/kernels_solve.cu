@@ -15,19 +15,33 @@
 
 // h_k = U^H Z[:, k] from the P partial rows of k_gdqr (hpart[b][k r + l]):
 // thread (l, slice s) adds rows b = s, s + S, ... as compensated FP32 pairs,
-// then lane l of the first warp adds the slices in order.  Every thread of
-// the block calls it; lanes l < R of warp 0 return h_k[l].
+// then lane l of the first warp adds the slices in order.  The rows are
+// loaded first (frame_h_load, before the Gram sums, so that their latency
+// overlaps that work) and reduced afterwards (frame_h); every thread of the
+// block calls both; lanes l < R of warp 0 return h_k[l].
+#define HMAX 16   // rows per thread: P <= HMAX NT / R for every R <= 16 (P <= 256)
 template <int R>
-static __device__ float2 frame_h(const float2 *hpart, int P, int q, int k, float4 *s_h) {
+static __device__ void frame_h_load(const float2 *hpart, int P, int q, int k, float2 (&v)[HMAX]) {
+    constexpr int S = NT / R;
+    const int t = threadIdx.x, l = t % R, s = t / R;
+#pragma unroll
+    for (int i = 0; i < HMAX; ++i) {
+        const int b = s + i * S;
+        v[i] = (s < S && b < P) ? __ldg(hpart + ((size_t)b * q + k) * R + l) : make_float2(0.f, 0.f);
+    }
+}
+template <int R>
+static __device__ float2 frame_h(const float2 (&v)[HMAX], int P, float4 *s_h) {
     constexpr int S = NT / R;
     const int t = threadIdx.x, l = t % R, s = t / R;
     if (s < S) {
         fsum2 re = {0.f, 0.f}, im = {0.f, 0.f};
-#pragma unroll 4
-        for (int b = s; b < P; b += S) {
-            const float2 v = __ldg(hpart + ((size_t)b * q + k) * R + l);
-            fsum_add(re, v.x);
-            fsum_add(im, v.y);
+#pragma unroll
+        for (int i = 0; i < HMAX; ++i) {
+            if (s + i * S < P) {
+                fsum_add(re, v[i].x);
+                fsum_add(im, v[i].y);
+            }
         }
         s_h[s * R + l] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
@@ -48,15 +62,15 @@ static __device__ float2 frame_h(const float2 *hpart, int P, int q, int k, float
 // The Cholesky solve of one frame's r x r system from its Gram pairs sP (FP64
 // sums) and h_k, by the block's first warp.
 template <int R>
-static __device__ void solve_frame(const double *sP, float2 *sG, float *sinv, bool any, const float2 *hpart, int P,
-                                   int q, int k, float4 *s_h, float2 *B, unsigned int *status) {
+static __device__ void solve_frame(const double *sP, float2 *sG, float *sinv, bool any, const float2 (&hv)[HMAX],
+                                   int P, int k, float4 *s_h, float2 *B, unsigned int *status) {
     constexpr int rr = R * R;
     for (int e = threadIdx.x; e < rr; e += blockDim.x) {
         const int a = e / R, b = e - a * R;
         const int p = a <= b ? pair_index(a, b, R) : pair_index(b, a, R);
         sG[e] = make_float2((float)sP[2 * p], (float)(a <= b ? sP[2 * p + 1] : -sP[2 * p + 1]));
     }
-    const float2 h = frame_h<R>(hpart, P, q, k, s_h);   // its barrier also publishes sG
+    const float2 h = frame_h<R>(hv, P, s_h);   // its barrier also publishes sG
     if ((threadIdx.x >> 5) != 0) return;
     const int lane = threadIdx.x & 31;
     const bool ok = any && warp_chol32<R>(sG, R, sinv);
@@ -79,12 +93,14 @@ __global__ void __launch_bounds__(NT) k_solve(const float2 *__restrict__ Prow, c
     __shared__ int s_rows[256];
     __shared__ float4 s_h[NT];
     const int k = blockIdx.x;
+    float2 hv[HMAX];
+    frame_h_load<R>(hpart, P, q, k, hv);
     const int lp = lineptr[k], L = lineptr[k + 1] - lp;
     for (int i = threadIdx.x; i < L; i += blockDim.x) s_rows[i] = framerows[lp + i];
     __syncthreads();
     // G_k pairs: sum over the frame's rows of the coil-summed row Grams
     block_sum(np, L, sP, [=](int p, int i) { return __ldg(Prow + (size_t)s_rows[i] * np + p); });
-    solve_frame<R>(sP, sG, sinv, L > 0, hpart, P, q, k, s_h, B, status);
+    solve_frame<R>(sP, sG, sinv, L > 0, hv, P, k, s_h, B, status);
 }
 
 // General masks: G_k = sum over the frame's samples s of the point Grams
@@ -115,6 +131,8 @@ __global__ void __launch_bounds__(NT) k_solve_gen(const double *__restrict__ par
     __shared__ float sinv[R];
     __shared__ float4 s_h[NT];
     const int k = blockIdx.x;
+    float2 hv[HMAX];
+    frame_h_load<R>(hpart, P, q, k, hv);
     const int m = fpk[k + 1] - fpk[k];
     for (int e = threadIdx.x; e < 2 * np; e += blockDim.x) {
         double acc = 0.0;
@@ -122,7 +140,7 @@ __global__ void __launch_bounds__(NT) k_solve_gen(const double *__restrict__ par
         sP[e] = acc;
     }
     __syncthreads();
-    solve_frame<R>(sP, sG, sinv, m > 0, hpart, P, q, k, s_h, B, status);
+    solve_frame<R>(sP, sG, sinv, m > 0, hv, P, k, s_h, B, status);
 }
 
 typedef void (*solve_kernel_t)(const float2 *, const float2 *, int, int, const int32_t *, const int32_t *, float2 *,
@@ -142,6 +160,7 @@ size_t frame_gram_part_count(int q, int rmax) { return (size_t)q * GEN_NCH * rma
 
 cudaError_t launch_solve(lrccs_ctx *c) {
     if (c->r < 1 || c->r > RMAXC) return cudaErrorInvalidValue;
+    if (c->gd_grid > HMAX * (NT / c->r)) return cudaErrorInvalidConfiguration;   // frame_h_load's reach
     if (c->general) {
         prof_begin(c, KID_SOLVE_GEN);
         kFrameGramGen[c->r - 1]<<<dim3(c->q, GEN_NCH), NT, 0, c->stream>>>(c->d_Pu, c->d_fpk, c->d_fu, c->d_fpart);
