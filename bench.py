@@ -41,7 +41,9 @@ T_ITER = 50
 METRIC = "altGDmin frame-iterations/s at NRMSE≤1e-3 vs FP64; p99 mini-batch latency"
 UNIT = "frame-iterations/s"
 FLUSH_BYTES = 256 << 20            # > 129 MB L2
-ITER_KERNELS = ["k_fwd_cols", "k_row_gram", "k_solve", "k_zb", "k_row_w", "k_adj_cols", "k_gdqr"]
+ITER_KERNELS = ["k_fwd_cols", "k_row_gram", "k_solve", "k_zb", "k_row_w", "k_adj_cols", "k_gdqr", "k_bstep"]
+# the separate line-mask kernels that k_bstep replaces when every sampled row fits one block
+SEPARATE_BSTEP = ("k_row_gram", "k_solve", "k_row_w", "k_zb")
 
 
 def dist_env():
@@ -91,12 +93,16 @@ def kernel_bytes(name, p, r, n_used):
         "k_gdqr": 6 * n * r + n * q,                     # read that, U, Z B^H, Z; write grad, U_{t+1}, U_t
         "k_zb": n * q + n * r,                           # read Z (B is tiny); write Z B^H
         "k_solve": 0,
+        "k_bstep": 2 * C * r * nu + n * q + n * r,       # sampled rows in once, T W out; Z in, Z B^H out
     }.get(name, 0)
     return 8 * b
 
 
-def iteration_bytes(p, r, n_used):
-    return sum(kernel_bytes(k, p, r, n_used) for k in ITER_KERNELS)
+def iteration_bytes(p, r, n_used, fused=True):
+    """Algorithmic bytes of one iteration: the fused B-step (k_bstep) or the
+    three separate kernels it replaces."""
+    skip = SEPARATE_BSTEP if fused else ("k_bstep",)
+    return sum(kernel_bytes(k, p, r, n_used) for k in ITER_KERNELS if k not in skip)
 
 
 def source_sha():
@@ -858,6 +864,7 @@ def main():
     n_used = int(p.mask.reshape(p.q, p.ny, p.nx)[:, :, 0].any(0).sum())
     it_stats = [d for d in stats if d["name"] in ITER_KERNELS and d["timed"] > 0]
     dominant = max(it_stats, key=lambda d: d["ms"])["name"]
+    fused = any(d["name"] == "k_bstep" and d["launches"] > 0 for d in stats)
     lrccs.lrccs_profile(s.ctx, dominant)
     step()                                    # untimed: the library re-captures its iteration graph
     torch.cuda.synchronize()
@@ -943,7 +950,7 @@ def main():
                 gpu_launches=launches, roofline=roof,
                 clocks=dict(sm_mhz=clk["sm_mhz"], sm_max_mhz=clk["sm_max_mhz"], reasons=clk["reasons"],
                             samples=clk["samples"]),
-                iteration_bytes=iteration_bytes(p, p.rank, n_used),
+                iteration_bytes=iteration_bytes(p, p.rank, n_used, fused=fused),
                 # the same timed solves split at the end of lrccs_init: the iterations alone
                 # (T graph-replayed iterations, init excluded) and the init per solve
                 iterations_only=dict(value=work * args.steps / ((tot_ms - init_ms) / 1e3), unit=UNIT,

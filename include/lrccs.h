@@ -112,9 +112,17 @@ typedef struct lrccs_params {
  *                 (even, divides nx, fwd_tx * r <= 256, and fits shared memory)
  *   coil_groups : coil groups (thread-block cluster size, 1..8) of the column
  *                 adjoint and the line-mask row passes
- *   row_groups  : coil groups (1..8) of the general-mask row transforms */
+ *   row_groups  : coil groups (1..8) of the general-mask row transforms
+ *   bstep_form  : line masks only.  0 (default): when every sampled k-space
+ *                 row of the iteration fits one block's shared memory and all
+ *                 rows' blocks can be resident at once, the row Grams, the
+ *                 per-frame solves (Alg. 2's B-step) and the row weighting of
+ *                 the gradient run as one cooperative launch (k_bstep);
+ *                 1: always the three separate kernels (k_row_gram, k_solve,
+ *                 k_row_w).  Both forms compute the same quantities; their
+ *                 FP32 summation order differs. */
 typedef struct lrccs_plan {
-    int32_t fwd_tx, coil_groups, row_groups, reserved;
+    int32_t fwd_tx, coil_groups, row_groups, bstep_form;
 } lrccs_plan;
 
 typedef struct lrccs_iter_info {
@@ -492,6 +500,17 @@ lrccs_status lrccs_forward_transform(lrccs_ctx *ctx, void *d_T, size_t bytes);
  * last block's exit and the spread of the entries, in ns.  enable == 0 with out == NULL frees the buffer.
  * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (out requested while off), LRCCS_E_NOMEM. */
 lrccs_status lrccs_gdqr_phases(lrccs_ctx *ctx, int32_t enable, double *out);
+
+/* Measurement support (the paper has no counterpart): phase times of the last
+ * fused line-mask B-step launch (k_bstep), recorded while lrccs_gdqr_phases
+ * timing is on.  out[22]: (mean, max over blocks) in ns of row load + Gram,
+ * first grid barrier, the first frame's Gram sum, the rest of the per-frame
+ * solves, second barrier, W_ky, row weighting, staging of the first Z chunk,
+ * the rest of Z B^H, block exit; then the
+ * first entry to last exit and the spread of the entries (ns).  Synchronises
+ * the context's stream.
+ * Errors: LRCCS_E_INVALID, LRCCS_E_STATE (timing off, or no fused launch). */
+lrccs_status lrccs_bstep_phases(lrccs_ctx *ctx, double *out);
 
 /* Test support for the bounded device waits (the paper has no counterpart).
  * With enable != 0 the next directly launched GD/QR kernel of this context (an

@@ -35,6 +35,7 @@ cudaError_t configure_kernels_gd(int max_smem);
 cudaError_t configure_kernels_general(int max_smem);
 cudaError_t configure_kernels_tc(int max_smem);
 cudaError_t configure_kernels_zh(int max_smem);
+cudaError_t configure_kernels_solve(int max_smem);
 
 #define CK(call)                                                                        \
     do {                                                                                \
@@ -250,6 +251,11 @@ static lrccs_status create_impl(const lrccs_dims *dims, const lrccs_params *para
     if (e == cudaSuccess) e = configure_kernels_general(optin);
     if (e == cudaSuccess) e = configure_kernels_tc(optin);
     if (e == cudaSuccess) e = configure_kernels_zh(optin);
+    if (e == cudaSuccess) e = configure_kernels_solve(optin);
+    if (e == cudaSuccess) {
+        c->nsm = nsm;
+        for (int rr = 1; rr <= 16; ++rr) c->bs_cap[rr] = rr <= rmax ? bstep_capacity(nc, c->nx, q, rr, optin, nsm) : 0;
+    }
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
@@ -1275,7 +1281,7 @@ const char *const kKernelNames[KID_COUNT] = {
     "k_eig", "k_u0", "k_gdqr", "k_fwd_cols", "k_row_gram", "k_solve", "k_row_w", "k_adj_cols",
     "k_images", "k_cg_init", "k_cg_step", "k_mean_resid", "k_union", "k_fill_general", "k_init_gen",
     "k_fwd_rows", "k_sample_gram", "k_solve_gen", "k_sample_w", "k_adj_rows", "k_mean_resid_gen", "k_mec_mask",
-    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_max", "k_b_operand", "k_zb"};
+    "k_mec_elem", "k_mec_tdft", "k_dft_a", "k_fwd_gemm", "k_tile_max", "k_b_operand", "k_zb", "k_bstep"};
 
 static cudaEvent_t get_event(lrccs_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -1699,14 +1705,51 @@ extern "C" lrccs_status lrccs_gdqr_phases(lrccs_ctx *c, int32_t enable, double *
         out[2 * (NCLK - 1) + 1] = (double)(e1 - e0);   // spread of the blocks' entries (ns)
     }
     if (enable && !c->d_gdts) {
-        if (!dalloc(c, &c->d_gdts, (size_t)G * NTS)) return LRCCS_E_NOMEM;
-        CK(cudaMemset(c->d_gdts, 0, (size_t)G * NTS * sizeof(long long)));
+        // k_gdqr's stamps, then k_bstep's (the same layout, after them)
+        if (!dalloc(c, &c->d_gdts, (size_t)2 * G * NTS)) return LRCCS_E_NOMEM;
+        CK(cudaMemset(c->d_gdts, 0, (size_t)2 * G * NTS * sizeof(long long)));
         drop_iter_graph(c);   // captured iterations take the stamps from now on
     } else if (!enable && c->d_gdts && !out) {
         drop_iter_graph(c);
         cudaFree(c->d_gdts);
         c->d_gdts = nullptr;
     }
+    return LRCCS_OK;
+}
+
+extern "C" lrccs_status lrccs_bstep_phases(lrccs_ctx *c, double *out) {
+    if (!c || !out) return LRCCS_E_INVALID;
+    if (!c->d_gdts) {
+        set_err(c, "lrccs_bstep_phases: phase timing is off");
+        return LRCCS_E_STATE;
+    }
+    // k_bstep's global-timer stamps (11 per block, for the blocks b < gd_grid
+    // that ran) follow k_gdqr's in the phase-timing buffer
+    const int G = c->gd_grid, NTS = 11, NST = 11;
+    const int nb = c->n_used < G ? c->n_used : G;
+    std::vector<long long> h((size_t)G * NTS);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(h.data(), c->d_gdts + (size_t)G * NTS, h.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    if (nb < 1) return LRCCS_E_STATE;
+    for (int i = 0; i + 1 < NST; ++i) {
+        double sum = 0.0, mx = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double d = (double)(h[(size_t)b * NST + i + 1] - h[(size_t)b * NST + i]);
+            sum += d;
+            mx = d > mx ? d : mx;
+        }
+        out[2 * i] = sum / nb;
+        out[2 * i + 1] = mx;
+    }
+    long long e0 = h[0], e1 = h[0], x1 = h[NST - 1];
+    for (int b = 0; b < nb; ++b) {
+        const long long e = h[(size_t)b * NST], x = h[(size_t)b * NST + NST - 1];
+        e0 = e < e0 ? e : e0;
+        e1 = e > e1 ? e : e1;
+        x1 = x > x1 ? x : x1;
+    }
+    out[2 * (NST - 1)] = (double)(x1 - e0);
+    out[2 * (NST - 1) + 1] = (double)(e1 - e0);
     return LRCCS_OK;
 }
 

@@ -395,18 +395,20 @@ LRCCS_DEV double warp_fsum(fsum2 v) {
 // e < nent, written as FP64 (re, im) pairs.  Thread (entry e, slice s) sums
 // items s, s + S, s + 2S, ... in that order with RB loads in flight, and the S
 // slices are then combined in order: deterministic, and one memory latency per
-// RB items instead of one per item.  All threads of the block (at most 256)
-// call it; it ends with a barrier.
+// RB items instead of one per item.  All threads of the block call it (the
+// first 256 do the work); it ends with a barrier.
 template <class F>
 LRCCS_DEV void block_sum(int nent, int nitem, double *dst, F fetch) {
     constexpr int RB = 16;
     __shared__ float4 s_acc[256];   // (hi, lo) of re and im per thread
-    const int t = threadIdx.x, nt = blockDim.x;
+    const int nt = blockDim.x < 256 ? (int)blockDim.x : 256;
+    const int t = threadIdx.x;
+    const bool act = t < nt;   // threads beyond the first 256 only meet the barriers
     const int S = nent >= nt ? 1 : max(1, min(nt / nent, nitem));
     for (int base = 0; base < nent; base += nt) {
         const int e = base + (S == 1 ? t : t % nent), s = S == 1 ? 0 : t / nent;
         fsum2 re = {0.f, 0.f}, im = {0.f, 0.f};
-        if (e < nent && s < S) {
+        if (act && e < nent && s < S) {
             for (int m = s; m < nitem; m += S * RB) {
                 float2 v[RB];
 #pragma unroll
@@ -422,13 +424,13 @@ LRCCS_DEV void block_sum(int nent, int nitem, double *dst, F fetch) {
             }
         }
         if (S == 1) {
-            if (e < nent) {
+            if (act && e < nent) {
                 dst[2 * e] = (double)re.hi + (double)re.lo;
                 dst[2 * e + 1] = (double)im.hi + (double)im.lo;
             }
             continue;
         }
-        s_acc[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        if (act) s_acc[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
         __syncthreads();
         if (t < nent) {
             fsum2 R = {0.f, 0.f}, I = {0.f, 0.f};
@@ -450,6 +452,35 @@ LRCCS_DEV void block_sum(int nent, int nitem, double *dst, F fetch) {
 // into dst (FP64 re, im pairs).
 LRCCS_DEV void block_reduce_rows(const float2 *part, int nblk, int len, double *dst) {
     block_sum(len, nblk, dst, [=](int e, int b) { return __ldcg(part + (size_t)b * len + e); });
+}
+
+// ---------------------------------------------------------------- grid barrier of a cooperative launch
+
+// Barrier number k (1, 2, ...) of this launch: wait until every block has
+// arrived k times (plus `skew` arrivals, which only the timeout test sets and
+// the grid can never make).  Bounded: gives up after `limit` polls (2^24, about
+// a second) and ORs `timeout_bit` into the status word; the kernel then runs on
+// to its end.
+LRCCS_DEV void grid_sync(unsigned int *bar, unsigned int k, unsigned int *status, unsigned int limit,
+                         unsigned int skew, unsigned int timeout_bit) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = k * gridDim.x + skew;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned int v = 0, spins = 0;
+        while (true) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if (++spins > limit) {
+                atomicOr(status, timeout_bit);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- asynchronous global -> shared copies

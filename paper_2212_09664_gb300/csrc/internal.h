@@ -35,8 +35,9 @@ enum {
 };
 
 // Grid-reduction counters.
-// CNT_BAR and CNT_BAR + 1: the grid-barrier and exit counters of k_gdqr.
-enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_COUNT = 8 };
+// CNT_BAR and CNT_BAR + 1: the grid-barrier and exit counters of k_gdqr;
+// CNT_BS_BAR and CNT_BS_BAR + 1: those of k_bstep.
+enum { CNT_ENERGY = 0, CNT_GRAMX0, CNT_BAR, CNT_BAR_EXIT, CNT_BS_BAR, CNT_BS_EXIT, CNT_COUNT = 8 };
 
 // Kernel ids (launch counting and optional CUDA-event timing).
 enum {
@@ -50,8 +51,8 @@ enum {
     KID_MEC_MASK, KID_MEC_ELEM, KID_MEC_TDFT,
     // precision forms of the forward transform (tcgen05 GEMM)
     KID_TC_A, KID_TC_GEMM, KID_TC_SCALE, KID_TC_B,
-    // Z B^H of the gradient
-    KID_ZB, KID_COUNT
+    // Z B^H of the gradient; the fused line-mask B-step
+    KID_ZB, KID_BSTEP, KID_COUNT
 };
 extern const char *const kKernelNames[KID_COUNT];
 
@@ -100,6 +101,8 @@ struct lrccs_ctx {
     int px, py;        // nx / 32, ny / 32
     int nblk;          // blocks of the pixel-parallel init kernels
     int gd_grid;       // blocks of the cooperative GD/QR kernel (all resident)
+    int nsm;           // multiprocessors of the device
+    int bs_cap[17];    // resident k_bstep<r> blocks for this shape, r = 1..16 (0: rows do not fit)
     int n_used;        // host copy of MT_NUSED
     int n_lines;       // host copy of MT_NLINES
     int m_max;         // host copy of MT_MMAX (largest per-frame sample count per coil)
@@ -241,6 +244,9 @@ cudaError_t launch_u0(lrccs_ctx *c);
 cudaError_t launch_gdqr(lrccs_ctx *c, int mode);      // F: GD step + Cholesky QR (mode 0: init U+)
 cudaError_t launch_zb(lrccs_ctx *c);                  // d_ZB <- Z B^H
 cudaError_t launch_solve(lrccs_ctx *c);                // C kernel
+bool bstep_fused_ok(const lrccs_ctx *c);               // k_bstep applies (line masks, rows resident)
+cudaError_t launch_bstep_fused(lrccs_ctx *c);          // B + C + D in one cooperative launch
+int bstep_capacity(int nc, int nx, int q, int r, int smem_optin, int nsm);
 cudaError_t launch_iteration(lrccs_ctx *c);            // A .. H for one iteration
 cudaError_t launch_images(lrccs_ctx *c, float2 *d_X);
 cudaError_t launch_normal_op(lrccs_ctx *c);           // U+ <- A^H A U, rank 1, b_k = 1

@@ -80,31 +80,7 @@ struct GdArgs {
 
 // ---------------------------------------------------------------- grid-wide steps
 
-// Barrier number k (1, 2, ...) of this launch: wait until every block has
-// arrived k times (plus `skew` arrivals, which only the timeout test sets and
-// the grid can never make).  Bounded: gives up after `limit` polls (2^24, about
-// a second) and raises ST_TIMEOUT; the kernel then runs on to its end.
-static __device__ void grid_sync(unsigned int *bar, unsigned int k, unsigned int *status, unsigned int limit,
-                                 unsigned int skew) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int target = k * gridDim.x + skew;
-        __threadfence();
-        atomicAdd(bar, 1u);
-        unsigned int v = 0, spins = 0;
-        while (true) {
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(bar) : "memory");
-            if (v >= target) break;
-            if (++spins > limit) {
-                atomicOr(status, (unsigned)ST_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
+// grid_sync (common.cuh) is the grid-wide barrier of this cooperative kernel.
 
 // Block b reduces entries e = b, b + G, b + 2G, ... (< len) of the G partial
 // rows part[g len + e], four entries at a time (128 threads each), into FP64
@@ -374,11 +350,11 @@ __global__ void __launch_bounds__(NTG, 1) k_gdqr(GdArgs a) {
         return (kind == 2 && iter ? np + rr : 0) + pair_index(x, y, r);
     });
     GD_TS(3);
-    grid_sync(a.bar, 1, a.status, a.spin_limit, a.bar_skew);
+    grid_sync(a.bar, 1, a.status, a.spin_limit, a.bar_skew, ST_TIMEOUT);
     GD_TS(4);
     grid_reduce(a.part, len1, a.tot);
     GD_TS(5);
-    grid_sync(a.bar, 2, a.status, a.spin_limit, a.bar_skew);
+    grid_sync(a.bar, 2, a.status, a.spin_limit, a.bar_skew, ST_TIMEOUT);
     GD_TS(6);
     for (int e = t; e < len1; e += NTG) {
         const double2 v = __ldcg(a.tot + e);

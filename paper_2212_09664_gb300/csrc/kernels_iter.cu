@@ -13,7 +13,9 @@
 // and by Parseval the row Gram FU^H FU of a row equals T^H T of the same row:
 // one iteration needs only the C r column transforms F_y and F_y^H.
 //
-// Kernels (one launch each per iteration; C is in kernels_solve.cu, I and F in kernels_gd.cu):
+// Kernels (one launch each per iteration; C is in kernels_solve.cu, I and F in kernels_gd.cu;
+// when every sampled row fits one block's shared memory, k_bstep in
+// kernels_solve.cu does B, C, D and I in one cooperative launch):
 //   A k_fwd_cols  : F_y of d_j o U over column tiles               -> T[j][ky][x][l] (sampled rows)
 //   B k_row_gram  : coil-summed row Gram sum_j T_j^H T_j per sampled row -> P[ky] (clusters)
 //   C k_solve     : G_k = sum of its rows' P, h_k (sum of k_gdqr's partial rows), Cholesky -> B
@@ -575,6 +577,12 @@ cudaError_t launch_iteration(lrccs_ctx *c) {
         if (el != cudaSuccess) return el;
         el = launch_iteration_general_back(c);
         if (el != cudaSuccess) return el;
+    } else if (bstep_fused_ok(c)) {
+        el = launch_bstep_fused(c);        // B + C + D + I (k_bstep, kernels_solve.cu)
+        if (el != cudaSuccess) return el;
+        el = launch_adj_cols(c);           // E
+        if (el != cudaSuccess) return el;
+        return launch_gdqr(c, 1);          // F
     } else {
         el = launch_row_gram(c);           // B
         if (el != cudaSuccess) return el;

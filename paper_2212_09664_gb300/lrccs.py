@@ -40,7 +40,7 @@ class Params(C.Structure):
 
 class Plan(C.Structure):
     _fields_ = [("fwd_tx", C.c_int32), ("coil_groups", C.c_int32), ("row_groups", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("bstep_form", C.c_int32)]
 
 
 class Ticket(C.Structure):
@@ -79,6 +79,7 @@ _sig = {
     "lrccs_set_state": (_st, [_vp, C.c_char_p, C.c_size_t]),
     "lrccs_test_wait_timeout": (_st, [_vp, C.c_int32]),
     "lrccs_gdqr_phases": (_st, [_vp, C.c_int32, C.POINTER(C.c_double)]),
+    "lrccs_bstep_phases": (_st, [_vp, C.POINTER(C.c_double)]),
     "lrccs_forward_transform": (_st, [_vp, _vp, C.c_size_t]),
     "lrccs_set_plan": (_st, [_vp, C.c_void_p]),
     "lrccs_get_plan": (_st, [_vp, C.c_void_p]),
@@ -324,6 +325,15 @@ def lrccs_gdqr_phases(ctx, enable: bool = True, read: bool = False):
     out = (C.c_double * 18)() if read else None
     _check(ctx, _lib.lrccs_gdqr_phases(ctx, 1 if enable else 0, out))
     return [(out[2 * i], out[2 * i + 1]) for i in range(9)] if read else None
+
+
+def lrccs_bstep_phases(ctx):
+    """Phase timing of the last fused B-step launch (lrccs_gdqr_phases on):
+    [(mean, max) ns] for each of the 10 intervals, then (first entry to last
+    exit, spread of the entries) in ns."""
+    out = (C.c_double * 22)()
+    _check(ctx, _lib.lrccs_bstep_phases(ctx, out))
+    return [(out[2 * i], out[2 * i + 1]) for i in range(11)]
 
 
 def lrccs_test_wait_timeout(ctx, enable: bool = True):

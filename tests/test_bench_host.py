@@ -22,7 +22,10 @@ def test_algorithmic_bytes_of_the_cardiac_workload():
     assert kb["k_adj_cols"] == 8 * (3409920 + 442368 + 368640)       # rows, maps in; n x r out
     assert kb["k_gdqr"] == 8 * (6 * 368640 + 1769472) == 31850496   # Gk, U, Z B^H, Z in; grad, U_t+1, U_t out
     assert kb["k_zb"] == 8 * (1769472 + 368640)                      # Z in, Z B^H out
-    assert bench.iteration_bytes(p, 10, n_used) == sum(kb.values())
+    assert kb["k_bstep"] == kb["k_row_w"] + kb["k_zb"]               # fused: rows in and out once, Z B^H
+    sep = sum(v for k, v in kb.items() if k != "k_bstep")
+    assert bench.iteration_bytes(p, 10, n_used, fused=False) == sep
+    assert bench.iteration_bytes(p, 10, n_used, fused=True) == sep - kb["k_row_gram"]
 
 
 class _FakeProc:

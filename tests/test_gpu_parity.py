@@ -221,6 +221,32 @@ def test_full_size_cardiac_all_50_iterates():
     g["solver"].close()
 
 
+def test_fused_and_separate_bstep_forms():
+    """Line masks: the row Grams, the per-frame solves and the row weighting run
+    as one cooperative launch (k_bstep) when every sampled row fits one block,
+    or as k_row_gram + k_solve + k_row_w (plan field bstep_form = 1).  Both
+    forms match the oracle per iterate, and the launch counts show which ran."""
+    p = synth.make_problem(MEDIUM, seed=31)
+    n_iter = 12
+    _, _, it = oracle_run(p, n_iter)
+    for form, ran, absent in ((0, "k_bstep", "k_row_gram"), (1, "k_row_gram", "k_bstep")):
+        s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank)
+        plan = lrccs.lrccs_get_plan(s.ctx)
+        plan.bstep_form = form
+        lrccs.lrccs_set_plan(s.ctx, plan)
+        s.init(*to_dev(p))
+        lrccs.lrccs_profile_reset(s.ctx)
+        errs = []
+        for t in range(n_iter):
+            s.iterate(1)
+            U, B = s.factors()
+            errs.append(nrmse((U @ B.T).cpu().numpy().astype(np.complex128), it["X"][t]))
+        launches = {d["name"]: d["launches"] for d in lrccs.lrccs_profile_read(s.ctx)}
+        assert launches[ran] == n_iter and launches[absent] == 0, (form, launches)
+        assert max(errs) < TOL, "form %d: per-iterate NRMSE %s" % (form, np.array2string(np.array(errs), precision=2))
+        s.close()
+
+
 @pytest.mark.parametrize("r", [5, 6, 7, 8, 9, 11, 12, 13, 14, 15, 16])
 def test_iterates_every_rank_instantiation(r):
     """The kernels are specialised per rank (1..16): each instantiation not
