@@ -231,15 +231,15 @@ cudaError_t launch_solve(lrccs_ctx *c) {
 #define BS_MAXC 32    // coils (one mbarrier each)
 
 // Phase A thread layout for rank R: the R x R Gram is cut into NB x NB blocks
-// of edge TB; the NU blocks on or above the diagonal each get WPG warps, whose
-// lanes stride over the row's C nx vectors and accumulate their block in
-// registers (NV floats, padded for the warp reduction).
+// of edge TB; the NU blocks on or above the diagonal each get a share of the
+// 16 warps in proportion to their work (bs_wstart), whose lanes stride over
+// the row's C nx vectors and accumulate their block in registers (NV floats,
+// padded for the warp reduction).
 template <int R>
 struct BsPlan {
     static constexpr int NB = (R + 4) / 5;
     static constexpr int TB = (R + NB - 1) / NB;
     static constexpr int NU = NB * (NB + 1) / 2;
-    static constexpr int WPG = (BS_NT / 32) / NU;
     static constexpr int NV = 2 * TB * TB <= 32 ? 32 : 64;
 };
 __host__ __device__ constexpr int bs_bi(int g, int nb) {
@@ -251,6 +251,52 @@ __host__ __device__ constexpr int bs_bj(int g, int nb) {
     int bi = 0;
     while (g >= nb - bi) { g -= nb - bi; ++bi; }
     return bi + g;
+}
+// complex MACs per vector of Gram block g: the upper triangle of a diagonal
+// block, all of an off-diagonal one, clipped at R
+__host__ __device__ constexpr int bs_work(int g, int R) {
+    const int nb = (R + 4) / 5, tb = (R + nb - 1) / nb, bi = bs_bi(g, nb), bj = bs_bj(g, nb);
+    int w = 0;
+    for (int i = 0; i < tb; ++i)
+        for (int j = 0; j < tb; ++j)
+            if (bi * tb + i < R && bj * tb + j < R && (bi != bj || j >= i)) ++w;
+    return w;
+}
+// First warp of group g (g = NU gives 16): one warp each, then every further
+// warp to the group with the most work per warp (lowest g on ties).
+__host__ __device__ constexpr int bs_wstart(int g, int R) {
+    const int nb = (R + 4) / 5, nu = nb * (nb + 1) / 2;
+    int al[10] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+    for (int used = nu; used < BS_NT / 32; ++used) {
+        int best = 0;
+        for (int u = 1; u < nu; ++u)
+            if (bs_work(u, R) * al[best] > bs_work(best, R) * al[u]) best = u;
+        ++al[best];
+    }
+    int st = 0;
+    for (int u = 0; u < g && u < nu; ++u) st += al[u];
+    return st;
+}
+
+// bs_wstart(g, R) for a runtime g, from constants folded at compile time
+template <int R, int U = 0>
+LRCCS_DEV int bs_ws(int g) {
+    if constexpr (U >= BsPlan<R>::NU) {
+        return BS_NT / 32;
+    } else {
+        constexpr int v = bs_wstart(U, R);
+        return g == U ? v : bs_ws<R, U + 1>(g);
+    }
+}
+// the Gram block whose warps include `warp`
+template <int R, int U = 0>
+LRCCS_DEV int bs_group_of(int warp) {
+    if constexpr (U + 1 >= BsPlan<R>::NU) {
+        return U;
+    } else {
+        constexpr int next = bs_wstart(U + 1, R);
+        return warp < next ? U : bs_group_of<R, U + 1>(warp);
+    }
 }
 
 // Elements [E0, E0 + N) of one R-vector in shared memory into registers
@@ -426,11 +472,9 @@ __global__ void __launch_bounds__(BS_NT, 1) k_bstep(const __grid_constant__ Bste
         float acc[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) acc[i] = 0.f;
-        const int g = warp / PL::WPG;
-        if (g < PL::NU) {
-            const int s = (warp - g * PL::WPG) * 32 + lane;
-            bs_gram_dispatch<R, 0>(g, row, nc, nx, s, PL::WPG * 32, s_mbar, 1u << 22, late, acc);
-        }
+        const int g = bs_group_of<R>(warp);
+        const int w0 = bs_ws<R>(g), nw = bs_ws<R>(g + 1) - w0;
+        bs_gram_dispatch<R, 0>(g, row, nc, nx, (warp - w0) * 32 + lane, nw * 32, s_mbar, 1u << 22, late, acc);
         bs_warp_reduce_scatter<NV>(acc, lane);
 #pragma unroll
         for (int u = 0; u < NV / 32; ++u) s_part[warp * 64 + lane * (NV / 32) + u] = acc[u];
@@ -445,7 +489,7 @@ __global__ void __launch_bounds__(BS_NT, 1) k_bstep(const __grid_constant__ Bste
         const int gi = bi * PL::NB - (bi * (bi - 1)) / 2 + (bj - bi);
         const int ent = (x - bi * TB) * TB + (y - bj * TB);
         float re = 0.f, im = 0.f;
-        for (int w = gi * PL::WPG; w < (gi + 1) * PL::WPG; ++w) {
+        for (int w = bs_ws<R>(gi); w < bs_ws<R>(gi + 1); ++w) {
             re += s_part[w * 64 + 2 * ent];
             im += s_part[w * 64 + 2 * ent + 1];
         }
@@ -552,15 +596,13 @@ __global__ void __launch_bounds__(BS_NT, 1) k_bstep(const __grid_constant__ Bste
     // ---- Z B^H for this block's share of the pixels (the data term of the
     // next gradient).  The pixels' Z rows are staged in chunks into the row
     // buffer (free after the weighting) with a row stride of 2 mod 16 complex
-    // values; thread pair (2p, 2p + 1) takes pixel p, the even and the odd
-    // frames, so that the 16 lanes of a half-warp read 16 distinct bank pairs
-    // of Z and two of B.  All R outputs stay in registers (B's rows are read
-    // as broadcasts) and the pair adds its halves by a shuffle.
+    // values, so that the 16 lanes of a half-warp read distinct bank pairs of
+    // Z.  Each thread keeps all R outputs of two pixels in registers, so every
+    // row of B read (a broadcast) serves two pixels.
     {
         const int per = (a.n + G - 1) / G, i0 = blockIdx.x * per, i1 = min(a.n, i0 + per);
         const int qs = bs_zstride(q);                // staged row stride
         const int cap = (nc * nx * R) / qs;          // pixels per chunk
-        const int half = t & 1;
         float2 *zs = row;
         for (int c0 = i0; c0 < i1; c0 += cap) {
             const int c1 = min(i1, c0 + cap), np_ = c1 - c0, cnt = np_ * q;
@@ -586,27 +628,42 @@ __global__ void __launch_bounds__(BS_NT, 1) k_bstep(const __grid_constant__ Bste
             cp_async_wait();
             __syncthreads();
             if (c0 == i0) BS_TS(8);
-            for (int pl = t >> 1; pl < ((np_ + 15) & ~15); pl += BS_NT / 2) {   // whole warps take part in the shuffle
-                const bool live = pl < np_;
-                float2 acc[R];
+            // thread (pixel pair pp, quarter m): pixels 2pp and 2pp + 1 of the
+            // chunk over the frames k = m, m + 4, ...; the four quarters are
+            // added by shuffles and lane m writes the outputs l = m, m + 4, ...
+            const int m4 = t & 3, npair = (np_ + 1) >> 1;
+            for (int pp = t >> 2; pp < ((npair + 7) & ~7); pp += BS_NT / 4) {   // whole warps take part
+                const int p0 = 2 * pp, p1 = p0 + 1;
+                const bool live0 = p0 < np_, live1 = p1 < np_;
+                float2 acc0[R], acc1[R];
 #pragma unroll
-                for (int l = 0; l < R; ++l) acc[l] = make_float2(0.f, 0.f);
-                if (live) {
-                    const float2 *zr = zs + pl * qs;
-                    for (int k = half; k < q; k += 2) {
-                        const float2 z = zr[k];
+                for (int l = 0; l < R; ++l) acc0[l] = acc1[l] = make_float2(0.f, 0.f);
+                if (live0) {
+                    const float2 *z0r = zs + p0 * qs, *z1r = zs + (live1 ? p1 : p0) * qs;
+                    for (int k = m4; k < q; k += 4) {
+                        const float2 z0 = z0r[k], z1 = live1 ? z1r[k] : make_float2(0.f, 0.f);
                         float2 br[R];
                         bs_load<R, 0, R>(sB + k * R, br);   // 16-byte loads for even R
 #pragma unroll
-                        for (int l = 0; l < R; ++l) cfma(acc[l], z, cconj(br[l]));
+                        for (int l = 0; l < R; ++l) {
+                            const float2 bc = cconj(br[l]);
+                            cfma(acc0[l], z0, bc);
+                            cfma(acc1[l], z1, bc);
+                        }
                     }
                 }
 #pragma unroll
-                for (int l = 0; l < R; ++l) acc[l] = cadd(acc[l], shfl_xor2(acc[l], 1));
-                if (live && half == 0) {
-                    float2 *dst = a.ZB + (size_t)(c0 + pl) * R;
+                for (int l = 0; l < R; ++l) {
+                    acc0[l] = cadd(acc0[l], shfl_xor2(acc0[l], 1));
+                    acc1[l] = cadd(acc1[l], shfl_xor2(acc1[l], 1));
+                    acc0[l] = cadd(acc0[l], shfl_xor2(acc0[l], 2));
+                    acc1[l] = cadd(acc1[l], shfl_xor2(acc1[l], 2));
+                }
 #pragma unroll
-                    for (int l = 0; l < R; ++l) dst[l] = acc[l];
+                for (int l = 0; l < R; ++l) {
+                    if ((l & 3) != m4) continue;
+                    if (live0) a.ZB[(size_t)(c0 + p0) * R + l] = acc0[l];
+                    if (live1) a.ZB[(size_t)(c0 + p1) * R + l] = acc1[l];
                 }
             }
         }
