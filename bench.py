@@ -811,6 +811,9 @@ def main():
     ap.add_argument("--no-comparators", action="store_true", help="skip the cuFFT / cuBLAS comparator timings")
     ap.add_argument("--no-radial", action="store_true", help="skip the 256 x 256 pseudo-radial workload leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-slice batched-form leg")
+    ap.add_argument("--bstep-form", type=int, default=0, choices=[0, 1],
+                    help="line-mask B-step of the headline solve: 0 fused (k_bstep) when the rows fit, "
+                         "1 the separate kernels (k_row_gram, k_solve, k_row_w, k_zb)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -845,6 +848,10 @@ def main():
     sm = torch.from_numpy(p.smaps).to(dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     s = lrccs.Solver(p.ny, p.nx, p.q, p.nc, p.rank, stream=stream)
+    if args.bstep_form:
+        plan = lrccs.lrccs_get_plan(s.ctx)
+        plan.bstep_form = args.bstep_form
+        lrccs.lrccs_set_plan(s.ctx, plan)
     U = torch.empty((p.n, p.rank), dtype=torch.complex64, device=dev)
     B = torch.empty((p.q, p.rank), dtype=torch.complex64, device=dev)
 
